@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the temporally blocked 3D 7-point Jacobi library on GB300.
+
+Default workload (what the headline metric is quoted on): FP64 512^3
+interior, interior U[0,1), halo 0 except the k=0 plane = 1, T = 100 sweeps
+per step (one step = one jacobi_sweep call = the whole hot path: halo copy,
+pass planning, all passes).  Metric: GLUP/s = nx*ny*nz*T / time (the
+paper's LUP/s, Sect. 1.2), and the fraction of the HBM roofline of Eq. (2),
+P0 = M_s / (2 s) per pass (16 B/LUP for FP64), effective d * P0 after
+temporal blocking.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   (the CPU oracle on the host cores)
+
+Under torchrun (N > 1) every rank sweeps its own replica of the workload
+(weak scaling; the method needs no exchange on one grid per GPU) and rank 0
+prints one JSON line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GLUP/s (3D 7-pt Jacobi) and % of HBM roofline, blocked vs plain, 1×GB300"
+M_S_FALLBACK = 6800.0  # GB/s, used only if MEASURED_PEAKS.json is absent
+# FP64 pipe of GB300: 1.25 TFLOP/s nominal counting an FMA as 2 flops, i.e.
+# 2 FP64 lanes per SM per clock (1.25e12 / (2 * 152 * 2.07e9)).
+FP64_LANES_PER_SM_CLK = 2
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+WORKLOADS = {
+    "fp64_512": dict(n=(512, 512, 512), dtype="f64", T=100, gen="dirichlet_z0", seed=2,
+                     name="jacobi3d_fp64_512cubed_T100_z0face1"),
+    "fp64_64": dict(n=(64, 64, 64), dtype="f64", T=10, gen="uniform", seed=1,
+                    name="jacobi3d_fp64_64cubed_T10"),
+    "fp32_1024": dict(n=(1024, 1024, 1024), dtype="f32", T=200, gen="mode", seed=3,
+                      name="jacobi3d_fp32_1024cubed_T200_mode16"),
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": M_S_FALLBACK}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1, 0
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    return dist, rank, ws, local
+
+
+def _make_grid(w, device):
+    import torch
+    from paper_1006_3148_gb300 import inputs
+    nx, ny, nz = w["n"]
+    dt = torch.float64 if w["dtype"] == "f64" else torch.float32
+    if w["gen"] == "dirichlet_z0":
+        return inputs.dirichlet_z0_grid(nx, ny, nz, w["seed"], dtype=dt, device=device)
+    if w["gen"] == "uniform":
+        return inputs.uniform_grid(nx, ny, nz, w["seed"], dtype=dt, device=device)
+    return inputs.mode_grid(nx, ny, nz, w["seed"], dtype=dt, device=device)
+
+
+def cpu_oracle_sample(w, budget_s: float):
+    """Times the CPU oracle (as it stands) on the host cores: the workload's
+    grid, sweeps in pairs until budget_s of CPU work.  Returns dict."""
+    import numpy as np
+    import oracle
+
+    nx, ny, nz = w["n"]
+    if w["dtype"] == "f32" and nx * ny * nz > 256 ** 3:
+        nx = ny = nz = 256  # bounded sample of the FP32 workload (same recipe)
+    ww = dict(w, n=(nx, ny, nz))
+    A = _make_grid(ww, "cpu").numpy()
+    B = np.empty_like(A)
+    oracle.jacobi(A, B, 2)  # first touch / warm
+    sweeps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.jacobi(A, B, 2)
+        sweeps += 2
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or sweeps >= w["T"]:
+            break
+    g = nx * ny * nz * sweeps / dt / 1e9
+    return {"value": g, "unit": "GLUP/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%dx%dx%d %s grid of the workload recipe, %d sweeps in %.1f s" % (
+                nx, ny, nz, w["dtype"], sweeps, dt)}
+
+
+def run_reference(args, w):
+    dist, rank, ws, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+
+    nx, ny, nz = w["n"]
+    A = _make_grid(w, "cpu").numpy()
+    B = np.empty_like(A)
+    per_step = 2  # bounded sample per step: 2 sweeps of the full grid
+    for _ in range(args.warmup):
+        oracle.jacobi(A, B, per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.jacobi(A, B, per_step)
+    dt = time.perf_counter() - t0
+    g = nx * ny * nz * per_step * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": g, "unit": "GLUP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": w["dtype"],
+        "data": "synthetic", "config": {"workload": w["name"], "nx": nx, "ny": ny, "nz": nz, "T": w["T"],
+                                        "sample": "%d sweeps per step" % per_step},
+        "cpu_baseline": {"value": g, "unit": "GLUP/s", "cores": oracle.threads(), "kind": "oracle",
+                         "sample": "%d sweeps per step of the %dx%dx%d grid" % (per_step, nx, ny, nz)},
+        "e2e": {"value": g, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, w):
+    import torch
+    from paper_1006_3148_gb300 import jacobi as J
+
+    dist, rank, ws, local = _dist()
+    if dist is not None:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nx, ny, nz = w["n"]
+    T = w["T"]
+    es = 8 if w["dtype"] == "f64" else 4
+    lups_step = nx * ny * nz * T
+    dt = torch.float64 if w["dtype"] == "f64" else torch.float32
+
+    h = J.Handle(nx, ny, nz, dt)
+    A = _make_grid(w, dev)
+    B = torch.empty_like(A)
+    tune_glups = None
+    if args.plan:
+        k, d, bx, by, bz = args.plan.split(":")
+        J.jacobi_set_plan(h, {"tb": J.KERNEL_TB, "plain": J.KERNEL_PLAIN}[k], int(d), int(bx), int(by), int(bz))
+    elif not args.no_tune:
+        sa, sb = torch.empty_like(A), torch.empty_like(A)
+        tune_glups = J.jacobi_tune(h, sa, sb)
+        del sa, sb
+        torch.cuda.empty_cache()
+    plan = J.jacobi_get_plan(h)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    J.jacobi_profile_enable(h, True)
+    for _ in range(args.warmup):
+        J.jacobi_sweep(h, A, B, T, stream)
+    barrier()
+    J.jacobi_profile_read(h)
+    sampler = ClockSampler(dev.index if dist is None else local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        J.jacobi_sweep(h, A, B, T, stream)
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = J.jacobi_profile_read(h)
+    assert J.jacobi_get_status(h) == 0, "device status word set during the timed region"
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * lups_step * args.steps / (ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (the pass kernel), live events
+    peaks, peak_src = _peaks()
+    m_s = float(peaks.get("hbm_gbs", M_S_FALLBACK))
+    n_pass = prof["pass_launches"]
+    pass_ms = prof["pass_ms"] / max(1, n_pass)
+    passes_per_step = n_pass / args.steps
+    lup_launch = nx * ny * nz * (T / passes_per_step)
+    bytes_launch = 2.0 * es * nx * ny * nz  # read src once, write dst once
+    hbm_ach = bytes_launch / (pass_ms * 1e-3) / 1e9
+    clk = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
+    roof = None
+    if w["dtype"] == "f64":
+        # 6 FP64 operations per LUP (5 additions + 1 division, Sect. 2.3's count)
+        alu_ach = 6.0 * lup_launch / (pass_ms * 1e-3) / 1e12
+        alu_peak = FP64_LANES_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 1e12
+        if alu_ach / alu_peak > hbm_ach / m_s:
+            roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": alu_ach / alu_peak, "traffic": None,
+                    "note": "FP64 pipe: 2 lanes/SM/clk x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s FMA-counted); "
+                            "achieved counts 6 FP64 ops per LUP",
+                    "hbm": {"achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
+                            "peak_source": peak_src}}
+    if roof is None:
+        roof = {"bound": "hbm", "achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
+                "traffic": None, "peak_source": peak_src}
+    roof["kernel"] = "tb_pass_kernel" if plan["kernel"] == J.KERNEL_TB else "plain_pass_kernel"
+    roof["avg_launch_ms"] = pass_ms
+    roof["sm_mhz_during"] = clk
+
+    p0 = m_s / (2.0 * es)  # Eq. (2) for element size es
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
+        "config": {"workload": w["name"], "nx": nx, "ny": ny, "nz": nz, "T": T, "plan": plan,
+                   "parallelism": "replicas" if ws > 1 else "single", "l2": "inputs larger than L2 "
+                   "(two %.2f GB grids)" % ((nx + 2) * (ny + 2) * (nz + 2) * es / 1e9)},
+        "hbm_roofline": {"P0_glups": p0, "per_pass_frac": value / ws / p0,
+                         "effective_frac": value / ws / (p0 * plan["depth"]), "M_s_gbs": m_s,
+                         "peak_source": peak_src},
+        "roofline": roof,
+        "gpu_launches": prof["pass_launches"] + prof["other_launches"],
+        "clocks": clocks,
+    }
+    if tune_glups is not None:
+        line["tuner_best_glups"] = tune_glups
+
+    # ---- plain single-pass baseline kernel (blocked vs plain), untimed in value
+    if rank == 0 and not args.no_plain:
+        hp = J.Handle(nx, ny, nz, dt)
+        J.jacobi_set_plan(hp, J.KERNEL_PLAIN)
+        Tp = min(T, 20)
+        J.jacobi_sweep(hp, A, B, Tp, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        J.jacobi_sweep(hp, A, B, Tp, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gp = nx * ny * nz * Tp / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        line["plain"] = {"value": gp, "unit": "GLUP/s", "sweeps": Tp, "per_pass_frac": gp / p0}
+        line["blocked_vs_plain"] = (value / ws) / gp
+        hp.close()
+
+    # ---- end to end through the host-buffer entry point
+    if not args.no_e2e:
+        host_in = A.cpu().pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        del A, B
+        torch.cuda.empty_cache()
+        J.jacobi_sweep_host(h, host_in, host_out, T, stream)
+        barrier()
+        ke = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            J.jacobi_sweep_host(h, host_in, host_out, T, stream)
+        dt_e = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt_e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt_e = float(t.item())
+        nbytes = host_in.numel() * es
+        line["e2e"] = {"value": ws * lups_step * ke / dt_e / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": nbytes, "steps": ke}
+
+    # ---- CPU oracle baseline on the host cores (rank 0, N = 1 only)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(w, args.cpu_budget)
+
+    h.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fp64_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--plan", default=None, help="force a plan, e.g. tb:4:64:16:64 or plain:1:1:1:1")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,161 @@
+/*
+ * jacobi.h -- C ABI of the GB300 (sm_103a) temporally blocked 3D Jacobi
+ * library (libjacobi.so).
+ *
+ * The operation (Sect. 1.1, Eq. 1): for every interior cell
+ *     B[i,j,k] = (A[i-1,j,k] + A[i+1,j,k] + A[i,j-1,k] + A[i,j+1,k]
+ *                 + A[i,j,k-1] + A[i,j,k+1]) / 6
+ * and successive sweeps write to grids A and B in turn.  Temporal blocking
+ * (Sect. 2.1: several updates per cell while it is on chip; Sect. 3.1: a
+ * subdomain with an h-layer halo takes h updates, update s on a region h-s
+ * layers wider) applies d sweeps per pass over HBM.
+ *
+ * Grid layout (every entry point): interior nx*ny*nz plus a one-cell
+ * Dirichlet halo, dense, x fastest:
+ *     idx(i,j,k) = (k*(ny+2) + j)*(nx+2) + i,   0 <= i <= nx+1, ...
+ * element type double (JACOBI_F64) or float (JACOBI_F32).  Halo cells are
+ * boundary values: read, never changed.
+ *
+ * Arithmetic: FP64 adds the six neighbours left to right in the order of
+ * Eq. (1) and divides the sum by 6.0 with IEEE round-to-nearest; results are
+ * bit-identical to a plain CPU loop doing the same.  FP32 adds in the same
+ * order and multiplies by RN_f32(1/6) (the paper's count of one
+ * multiplication and five additions per update, Sect. 2.3).
+ *
+ * Ownership and errors: the caller owns every grid buffer (device memory of
+ * the current device, 16-byte aligned); the library owns handles and its
+ * own scratch.  Every call returns an int status, JACOBI_OK (0) or a
+ * negative JACOBI_ERR_* code; no call aborts or prints.  Device work is
+ * enqueued on the caller's stream (cudaStream_t passed as jacobi_stream_t;
+ * NULL = legacy default stream) with no implicit device synchronisation
+ * unless stated.  Calls on one handle must not overlap on different streams.
+ */
+#ifndef JACOBI_H
+#define JACOBI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so that this header needs no
+ * CUDA header. */
+typedef struct CUstream_st *jacobi_stream_t;
+
+typedef enum { JACOBI_F64 = 0, JACOBI_F32 = 1 } jacobi_dtype;
+
+enum {
+    JACOBI_OK = 0,
+    JACOBI_ERR_ARG = -1,           /* bad size, count, pointer or option      */
+    JACOBI_ERR_DTYPE = -2,         /* dtype not JACOBI_F64 / JACOBI_F32       */
+    JACOBI_ERR_ALLOC = -3,         /* device or host allocation failed        */
+    JACOBI_ERR_CUDA = -4,          /* a CUDA call failed (see last_cuda_error) */
+    JACOBI_ERR_TIMEOUT = -5,       /* a device-side wait ran out its limit    */
+    JACOBI_ERR_BOUNDS = -6,        /* a device-side index check failed        */
+    JACOBI_ERR_NOT_CONVERGED = -7, /* refinement stopped at max_outer         */
+    JACOBI_ERR_ALIGN = -8,         /* grid pointer not 16-byte aligned        */
+    JACOBI_ERR_UNSUPPORTED = -9    /* plan not launchable on this device      */
+};
+
+/* Kernel families selectable by jacobi_set_plan. */
+enum {
+    JACOBI_KERNEL_AUTO = 0,  /* tuned (or default) plan                      */
+    JACOBI_KERNEL_PLAIN = 1, /* one sweep per launch, every operand from
+                                global memory: the single-pass baseline       */
+    JACOBI_KERNEL_TB = 2     /* z-streaming pass; depth d > 1 runs the
+                                time-skewed cluster pipeline                  */
+};
+
+typedef struct jacobi_plan_s *jacobi_h;
+typedef struct jacobi_batch_s *jacobi_batch_h;
+
+/* Text of a status code (static storage, never NULL). */
+const char *jacobi_status_string(int status);
+/* Library version as major*10000 + minor*100 + patch. */
+int jacobi_version(void);
+/* Text of the last CUDA error seen by this thread's calls ("" if none). */
+const char *jacobi_last_cuda_error(void);
+
+/* Creates a handle for grids of interior nx*ny*nz (each >= 1, and
+ * (nx+2)(ny+2)(nz+2) < 2^40 elements) of element type dtype, on the current
+ * device.  Allocates a 4-byte device status word.  *out is set to NULL on
+ * error. */
+int jacobi_create(jacobi_h *out, int nx, int ny, int nz, int dtype);
+
+/* Frees the handle.  The caller must have synchronised every stream that
+ * has work of this handle in flight.  NULL is accepted. */
+int jacobi_destroy(jacobi_h h);
+
+/* Applies T >= 0 sweeps of Eq. (1), grids A and B in turn (Sect. 1.1).
+ * First copies the halo of A into B (so both carry the same Dirichlet
+ * values), then runs ceil-ish(T/d) passes of depth <= d, pass p reading the
+ * grid written by pass p-1.  The number of passes always has the parity of
+ * T, so the result is in B if T is odd and in A if T is even, exactly as
+ * with single sweeps; the other grid's interior is left unspecified.  T = 0
+ * does nothing.  A and B: device pointers, 16-byte aligned, not
+ * overlapping, each (nx+2)(ny+2)(nz+2) elements.  Asynchronous on stream.
+ * Device-side wait timeouts are reported by jacobi_get_status. */
+int jacobi_sweep(jacobi_h h, void *A, void *B, int T, jacobi_stream_t stream);
+
+/* Same operation with host buffers (end-to-end entry point): copies
+ * A_host (pageable or pinned, (nx+2)(ny+2)(nz+2) elements) to library-owned
+ * device grids (allocated on first use, freed by jacobi_destroy), runs
+ * jacobi_sweep, and copies the result grid back to out_host.  Synchronises
+ * stream before returning. */
+int jacobi_sweep_host(jacobi_h h, const void *A_host, void *out_host, int T,
+                      jacobi_stream_t stream);
+
+/* Forces a plan: kernel (JACOBI_KERNEL_*), temporal depth (1..16; 1 for
+ * PLAIN), tile interior bx*by (bx, by >= 1) and z chunk bz >= 1 interior
+ * planes per cluster (ignored by PLAIN).  Depths > 8 need the non-portable
+ * cluster size.  JACOBI_KERNEL_AUTO returns to the tuned/default plan.
+ * Returns JACOBI_ERR_UNSUPPORTED if the plan cannot launch on this device
+ * (shared memory, registers, cluster occupancy). */
+int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz);
+
+/* Reads back the plan jacobi_sweep will use. */
+int jacobi_get_plan(jacobi_h h, int *kernel, int *depth, int *bx, int *by, int *bz);
+
+/* Autotuner (experiment-driven parameter choice, Sect. 2.4): times candidate
+ * plans (depth 1..8, tile shapes, z chunks) on the caller's scratch grids
+ * (same size as the handle's grids; contents overwritten, never the user's
+ * data) and keeps the fastest as the handle's AUTO plan.  Results are
+ * cached per process by (dtype, nx, ny, nz, SM count).  Synchronises
+ * stream.  *glups (may be NULL) receives the best measured GLUP/s. */
+int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stream,
+                double *glups);
+
+/* Pass planning (host only, no device work): splits T >= 0 sweeps into
+ * passes of depth <= depth (>= 1) whose count has the parity of T, as even
+ * as possible (a team sweep of Sect. 2.1 applies t*T updates; here a pass
+ * applies d).  Writes the depths to depths[0..n-1] and returns n, or -1 if
+ * more than max_passes passes would be needed or an argument is bad. */
+int jacobi_plan_passes(int T, int depth, int *depths, int max_passes);
+
+/* Reads and clears the handle's device status word (synchronises the
+ * device).  *device_status: 0 = fine, else the first JACOBI_ERR_* code a
+ * kernel recorded (JACOBI_ERR_TIMEOUT, JACOBI_ERR_BOUNDS). */
+int jacobi_get_status(jacobi_h h, int *device_status);
+
+/* Kernel timing for benchmarks.  While enabled, every pass-kernel launch of
+ * this handle is bracketed by two CUDA events recorded on the launch
+ * stream, and every other kernel launch is counted.  enable = 0 stops
+ * recording (already recorded launches stay until read). */
+int jacobi_profile_enable(jacobi_h h, int enable);
+
+/* Synchronises the recorded events and returns, since the previous read:
+ * *pass_ms = summed device time of the pass launches (ms), *pass_launches,
+ * *other_launches (halo copies and other helper kernels).  Resets the
+ * record.  Any output pointer may be NULL. */
+int jacobi_profile_read(jacobi_h h, double *pass_ms, int *pass_launches, int *other_launches);
+
+/* Test hook for failure detection: mode 1 makes the next pass kernel omit
+ * one mbarrier arrival so that its bounded waits run out (after
+ * limit_ms milliseconds); the kernel records JACOBI_ERR_TIMEOUT and returns
+ * without faulting.  mode 0 disables it.  limit_ms also sets the wait limit
+ * of later launches (default 2000). */
+int jacobi_debug_set_fault(jacobi_h h, int mode, int limit_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JACOBI_H */

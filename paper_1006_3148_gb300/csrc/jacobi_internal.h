@@ -1,0 +1,61 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/jacobi.h"
+
+namespace jac {
+
+// Arguments of one temporally blocked pass (one launch).
+struct TbArgs {
+    const void *src;
+    void *dst;
+    int nx, ny, nz;     // interior size
+    int depth;          // D: levels per pass = CTAs per cluster
+    int bx, by, bz;     // tile interior (x, y) and z chunk (interior planes)
+    int ntx;            // number of x tiles (grid.x = D * ntx)
+    int W, H, Wp;       // ring plane: width bx+2D, height by+2D, padded pitch
+    int R;              // ring slots per CTA
+    int *status;        // device status word (first error code wins)
+    unsigned long long limit_ns;  // bound of every device-side wait
+    int fault_mode;     // test hook: 1 = drop one arrival (see jacobi.h)
+};
+
+struct PlainArgs {
+    const void *src;
+    void *dst;
+    int nx, ny, nz;
+    int kz;  // planes per thread
+};
+
+// Plan of one handle.
+struct Plan {
+    int kernel = JACOBI_KERNEL_TB;
+    int depth = 1;
+    int bx = 64, by = 16, bz = 64;
+};
+
+// Launch resources of a TB plan (host side), filled by tb_configure.
+struct TbLaunch {
+    int nc = 0, maxc = 0;   // compute threads, cells per thread (template)
+    size_t smem = 0;        // dynamic shared memory bytes
+    int R = 4;
+    int W = 0, H = 0, Wp = 0;
+};
+
+constexpr int kTbThreadsLoader = 32;
+
+// Kernels (sweep_kernels.cu).  All return cudaError_t of the launch.
+cudaError_t tb_configure(int dtype, int depth, int bx, int by, TbLaunch *out);
+cudaError_t tb_launch(int dtype, const TbArgs &a, const TbLaunch &L, cudaStream_t s);
+cudaError_t tb_max_clusters(int dtype, const TbLaunch &L, int depth, int *clusters);
+cudaError_t plain_launch(int dtype, const PlainArgs &a, cudaStream_t s);
+cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, int nz, cudaStream_t s);
+
+// Pass planning: split T sweeps into passes of depth <= d whose count has
+// the parity of T (so the result ends in the grid single sweeps would use).
+int plan_passes(int T, int d, int *depths, int max_passes);
+
+}  // namespace jac

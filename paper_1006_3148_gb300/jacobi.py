@@ -1,0 +1,217 @@
+"""Python binding of libjacobi.so: the C ABI's entry points under the same
+names, taking torch tensors (device memory) and torch streams.
+
+Argument marshalling only -- every step of a sweep runs in the library's
+CUDA kernels.  There is no fallback: if libjacobi.so is missing or cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+F64 = 0
+F32 = 1
+KERNEL_AUTO, KERNEL_PLAIN, KERNEL_TB = 0, 1, 2
+
+STATUS = {
+    0: "JACOBI_OK", -1: "JACOBI_ERR_ARG", -2: "JACOBI_ERR_DTYPE", -3: "JACOBI_ERR_ALLOC",
+    -4: "JACOBI_ERR_CUDA", -5: "JACOBI_ERR_TIMEOUT", -6: "JACOBI_ERR_BOUNDS",
+    -7: "JACOBI_ERR_NOT_CONVERGED", -8: "JACOBI_ERR_ALIGN", -9: "JACOBI_ERR_UNSUPPORTED",
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class JacobiError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = "%s failed: %s (%d)" % (what, STATUS.get(code, "?"), code)
+        if code == -4 and _lib is not None:
+            msg += ": " + _lib.jacobi_last_cuda_error().decode()
+        super().__init__(msg)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libjacobi.so (building it first if allowed and needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libjacobi.so not built (%s); run __graft_entry__.build()" % _build.LIB)
+        L = ctypes.CDLL(_build.LIB)
+        P, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        pi = ctypes.POINTER(ctypes.c_int)
+        sig = {
+            "jacobi_status_string": ([i], ctypes.c_char_p),
+            "jacobi_version": ([], i),
+            "jacobi_last_cuda_error": ([], ctypes.c_char_p),
+            "jacobi_create": ([ctypes.POINTER(P), i, i, i, i], i),
+            "jacobi_destroy": ([P], i),
+            "jacobi_sweep": ([P, P, P, i, P], i),
+            "jacobi_sweep_host": ([P, P, P, i, P], i),
+            "jacobi_set_plan": ([P, i, i, i, i, i], i),
+            "jacobi_get_plan": ([P, pi, pi, pi, pi, pi], i),
+            "jacobi_tune": ([P, P, P, P, ctypes.POINTER(d)], i),
+            "jacobi_get_status": ([P, pi], i),
+            "jacobi_debug_set_fault": ([P, i, i], i),
+            "jacobi_plan_passes": ([i, i, pi, i], i),
+            "jacobi_profile_enable": ([P, i], i),
+            "jacobi_profile_read": ([P, ctypes.POINTER(d), pi, pi], i),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return L
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise JacobiError(code, what)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dtype_code(dtype) -> int:
+    if dtype in (torch.float64, F64, "f64", "float64"):
+        return F64
+    if dtype in (torch.float32, F32, "f32", "float32"):
+        return F32
+    raise ValueError("dtype must be float64 or float32")
+
+
+def _grid_ptr(t: torch.Tensor, shape, dtype) -> ctypes.c_void_p:
+    if not t.is_cuda or not t.is_contiguous() or t.dtype != dtype or tuple(t.shape) != tuple(shape):
+        raise ValueError("grid must be a contiguous CUDA %s tensor of shape %s" % (dtype, shape))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Handle:
+    """Owns a jacobi_h.  Grids are tensors shaped (nz+2, ny+2, nx+2)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, dtype=torch.float64):
+        L = load()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.dtype = torch.float64 if _dtype_code(dtype) == F64 else torch.float32
+        self.shape = (self.nz + 2, self.ny + 2, self.nx + 2)
+        h = ctypes.c_void_p()
+        _check(L.jacobi_create(ctypes.byref(h), self.nx, self.ny, self.nz, _dtype_code(dtype)), "jacobi_create")
+        self._h = h
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().jacobi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def jacobi_create(nx, ny, nz, dtype=torch.float64) -> Handle:
+    return Handle(nx, ny, nz, dtype)
+
+
+def jacobi_destroy(h: Handle):
+    h.close()
+
+
+def jacobi_sweep(h: Handle, A: torch.Tensor, B: torch.Tensor, T: int, stream=None) -> torch.Tensor:
+    """T sweeps of Eq. (1), A and B in turn; returns the grid holding the
+    result (B if T is odd, A if even)."""
+    pa = _grid_ptr(A, h.shape, h.dtype)
+    pb = _grid_ptr(B, h.shape, h.dtype)
+    _check(load().jacobi_sweep(h.ptr, pa, pb, int(T), _stream(stream)), "jacobi_sweep")
+    return B if T % 2 == 1 else A
+
+
+def jacobi_sweep_host(h: Handle, A_host: torch.Tensor, out_host: torch.Tensor, T: int, stream=None):
+    for t in (A_host, out_host):
+        if t.is_cuda or not t.is_contiguous() or t.dtype != h.dtype or tuple(t.shape) != h.shape:
+            raise ValueError("host grids must be contiguous CPU tensors of shape %s" % (h.shape,))
+    _check(load().jacobi_sweep_host(h.ptr, ctypes.c_void_p(A_host.data_ptr()),
+                                    ctypes.c_void_p(out_host.data_ptr()), int(T), _stream(stream)),
+           "jacobi_sweep_host")
+    return out_host
+
+
+def jacobi_set_plan(h: Handle, kernel: int, depth: int = 1, bx: int = 64, by: int = 16, bz: int = 64):
+    _check(load().jacobi_set_plan(h.ptr, int(kernel), int(depth), int(bx), int(by), int(bz)),
+           "jacobi_set_plan")
+
+
+def jacobi_get_plan(h: Handle) -> dict:
+    v = [ctypes.c_int() for _ in range(5)]
+    _check(load().jacobi_get_plan(h.ptr, *[ctypes.byref(x) for x in v]), "jacobi_get_plan")
+    return dict(zip(("kernel", "depth", "bx", "by", "bz"), (x.value for x in v)))
+
+
+def jacobi_tune(h: Handle, scratchA: torch.Tensor, scratchB: torch.Tensor, stream=None) -> float:
+    g = ctypes.c_double()
+    _check(load().jacobi_tune(h.ptr, _grid_ptr(scratchA, h.shape, h.dtype), _grid_ptr(scratchB, h.shape, h.dtype),
+                              _stream(stream), ctypes.byref(g)), "jacobi_tune")
+    return g.value
+
+
+def jacobi_get_status(h: Handle) -> int:
+    v = ctypes.c_int()
+    _check(load().jacobi_get_status(h.ptr, ctypes.byref(v)), "jacobi_get_status")
+    return v.value
+
+
+def jacobi_debug_set_fault(h: Handle, mode: int, limit_ms: int = 2000):
+    _check(load().jacobi_debug_set_fault(h.ptr, int(mode), int(limit_ms)), "jacobi_debug_set_fault")
+
+
+def jacobi_status_string(code: int) -> str:
+    return load().jacobi_status_string(int(code)).decode()
+
+
+def jacobi_plan_passes(T: int, depth: int) -> list:
+    buf = (ctypes.c_int * (max(T, 1) + 1))()
+    n = load().jacobi_plan_passes(int(T), int(depth), buf, max(T, 1) + 1)
+    if n < 0:
+        raise JacobiError(-1, "jacobi_plan_passes")
+    return list(buf[:n])
+
+
+def jacobi_profile_enable(h: Handle, enable: bool = True):
+    _check(load().jacobi_profile_enable(h.ptr, 1 if enable else 0), "jacobi_profile_enable")
+
+
+def jacobi_profile_read(h: Handle) -> dict:
+    ms, npass, nother = ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+    _check(load().jacobi_profile_read(h.ptr, ctypes.byref(ms), ctypes.byref(npass), ctypes.byref(nother)),
+           "jacobi_profile_read")
+    return {"pass_ms": ms.value, "pass_launches": npass.value, "other_launches": nother.value}

@@ -1,0 +1,163 @@
+"""GPU parity of jacobi_sweep against the CPU oracle (through the C ABI).
+
+FP64 must be bit-identical (fixed left-to-right sum, division by 6.0).
+FP32 is compared bitwise against the oracle's FP32 loop (same operation
+order) and within 1e-5 * max|u| against the FP64 oracle run on the widened
+FP32 inputs.
+"""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1006_3148_gb300 import inputs
+from paper_1006_3148_gb300 import jacobi as J
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=None)
+def _input(shape, seed, dtype):
+    nx, ny, nz = shape
+    return inputs.uniform_grid(nx, ny, nz, seed, dtype=torch.float64).to(dtype)
+
+
+@functools.lru_cache(maxsize=None)
+def _expected(shape, seed, dtype, T):
+    a = _input(shape, seed, dtype).numpy()
+    return oracle.jacobi_result(a, T)
+
+
+def _gpu(shape, seed, dtype, T, plan=None, A0=None):
+    nx, ny, nz = shape
+    h = J.Handle(nx, ny, nz, dtype)
+    if plan is not None:
+        J.jacobi_set_plan(h, *plan)
+    A = (A0 if A0 is not None else _input(shape, seed, dtype)).cuda()
+    B = torch.full_like(A, float("nan"))
+    out = J.jacobi_sweep(h, A, B, T)
+    torch.cuda.synchronize()
+    assert J.jacobi_get_status(h) == 0
+    h.close()
+    return out.cpu().numpy()
+
+
+SHAPES = [(1, 1, 1), (2, 3, 1), (5, 4, 3), (7, 9, 11), (13, 6, 17), (33, 31, 29), (67, 45, 33)]
+PLANS = [
+    (J.KERNEL_PLAIN, 1, 1, 1, 1),
+    (J.KERNEL_TB, 1, 4, 3, 2),
+    (J.KERNEL_TB, 1, 8, 8, 8),
+    (J.KERNEL_TB, 1, 64, 16, 64),
+    (J.KERNEL_TB, 2, 4, 4, 3),
+    (J.KERNEL_TB, 3, 8, 5, 4),
+    (J.KERNEL_TB, 4, 16, 8, 7),
+    (J.KERNEL_TB, 5, 5, 7, 9),
+    (J.KERNEL_TB, 8, 32, 16, 16),
+    (J.KERNEL_TB, 8, 3, 3, 2),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("plan", PLANS, ids=lambda p: "k%d_d%d_%dx%dx%d" % p)
+def test_fp64_bit_exact_small(shape, plan):
+    for T in (1, 2, 3, 7, 12):
+        got = _gpu(shape, 11, torch.float64, T, plan)
+        exp = _expected(shape, 11, torch.float64, T)
+        assert np.array_equal(got, exp), (shape, plan, T, np.abs(got - exp).max())
+
+
+@pytest.mark.parametrize("shape", [(5, 4, 3), (33, 31, 29), (67, 45, 33)])
+@pytest.mark.parametrize("plan", [PLANS[0], PLANS[3], PLANS[6], PLANS[8]], ids=lambda p: "k%d_d%d" % p[:2])
+def test_fp32_bitwise_vs_fp32_oracle_and_tolerance_vs_fp64(shape, plan):
+    for T in (1, 4, 9):
+        got = _gpu(shape, 12, torch.float32, T, plan)
+        exp32 = _expected(shape, 12, torch.float32, T)
+        assert np.array_equal(got, exp32), (shape, plan, T)
+        a64 = _input(shape, 12, torch.float32).to(torch.float64).numpy()
+        exp64 = oracle.jacobi_result(a64, T)
+        assert np.abs(got.astype(np.float64) - exp64).max() <= 1e-5 * np.abs(exp64).max()
+
+
+def test_workload_64cubed_fp64_all_depths():
+    # 64^3 interior, interior and halo U[0,1) from seed 1, T = 10
+    shape = (64, 64, 64)
+    exp = _expected(shape, 1, torch.float64, 10)
+    for plan in [None, (J.KERNEL_PLAIN, 1, 1, 1, 1)] + [(J.KERNEL_TB, d, 32, 16, 32) for d in (1, 2, 4, 8)]:
+        got = _gpu(shape, 1, torch.float64, 10, plan)
+        assert np.array_equal(got, exp), plan
+
+
+def test_t_zero_is_noop_and_parity():
+    shape = (9, 8, 7)
+    A0 = _input(shape, 3, torch.float64)
+    h = J.Handle(*shape, torch.float64)
+    A = A0.cuda()
+    B = torch.zeros_like(A)
+    assert J.jacobi_sweep(h, A, B, 0) is A
+    assert torch.equal(A.cpu(), A0) and torch.count_nonzero(B) == 0
+    out = J.jacobi_sweep(h, A, B, 5)
+    assert out is B
+    halo = torch.ones(A.shape, dtype=torch.bool)
+    halo[1:-1, 1:-1, 1:-1] = False
+    assert torch.equal(B.cpu()[halo], A0[halo]) and torch.equal(A.cpu()[halo], A0[halo])
+
+
+def test_argument_errors():
+    h = J.Handle(8, 8, 8, torch.float64)
+    A = torch.zeros(h.shape, dtype=torch.float64, device="cuda")
+    B = torch.zeros_like(A)
+    L = J.load()
+    s = J._stream(None)
+    import ctypes
+    pa, pb = ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr())
+    assert L.jacobi_sweep(h.ptr, pa, pb, -1, s) == -1
+    assert L.jacobi_sweep(h.ptr, pa, pa, 1, s) == -1
+    assert L.jacobi_sweep(h.ptr, ctypes.c_void_p(A.data_ptr() + 8), pb, 1, s) == -8
+    assert L.jacobi_sweep(h.ptr, pa, ctypes.c_void_p(A.data_ptr() + 16), 1, s) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 0, 8, 8, 8) == -1
+    assert L.jacobi_set_plan(h.ptr, 9, 1, 8, 8, 8) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 8, 512, 512, 8) == -9
+
+
+def test_bounded_wait_timeout_reports_status_and_context_survives():
+    # Failure detection without a fault: the test hook drops one mbarrier
+    # arrival; every wait is bounded, so the kernel records TIMEOUT and exits.
+    shape = (40, 24, 30)
+    h = J.Handle(*shape, torch.float64)
+    J.jacobi_set_plan(h, J.KERNEL_TB, 2, 16, 8, 10)
+    A = _input(shape, 4, torch.float64).cuda()
+    B = torch.zeros_like(A)
+    J.jacobi_debug_set_fault(h, 1, 50)
+    J.jacobi_sweep(h, A, B, 2)
+    torch.cuda.synchronize()
+    assert J.jacobi_get_status(h) == -5
+    # the context is still usable and the next sweep is exact
+    A = _input(shape, 4, torch.float64).cuda()
+    out = J.jacobi_sweep(h, A, B, 2)
+    torch.cuda.synchronize()
+    assert J.jacobi_get_status(h) == 0
+    assert np.array_equal(out.cpu().numpy(), _expected(shape, 4, torch.float64, 2))
+
+
+def test_host_entry_point_matches_oracle():
+    shape = (30, 20, 25)
+    h = J.Handle(*shape, torch.float64)
+    A0 = _input(shape, 6, torch.float64).pin_memory()
+    out = torch.empty_like(A0).pin_memory()
+    J.jacobi_sweep_host(h, A0, out, 7)
+    assert np.array_equal(out.numpy(), _expected(shape, 6, torch.float64, 7))
+
+
+def test_tuner_picks_a_plan_and_result_is_plan_independent():
+    shape = (96, 80, 72)
+    h = J.Handle(*shape, torch.float64)
+    sa = torch.zeros(h.shape, dtype=torch.float64, device="cuda")
+    sb = torch.zeros_like(sa)
+    g = J.jacobi_tune(h, sa, sb)
+    assert g > 0
+    p = J.jacobi_get_plan(h)
+    assert p["kernel"] == J.KERNEL_TB and 1 <= p["depth"] <= 8
+    got = _gpu(shape, 7, torch.float64, 9)
+    assert np.array_equal(got, _expected(shape, 7, torch.float64, 9))

@@ -212,8 +212,10 @@ def run_ours(args, w):
     B = torch.empty_like(A)
     tune_glups = None
     if args.plan:
-        k, d, bx, by, bz = args.plan.split(":")
-        J.jacobi_set_plan(h, {"tb": J.KERNEL_TB, "plain": J.KERNEL_PLAIN}[k], int(d), int(bx), int(by), int(bz))
+        f = args.plan.split(":")
+        ring = int(f[5]) if len(f) > 5 else 0
+        J.jacobi_set_plan(h, {"tb": J.KERNEL_TB, "plain": J.KERNEL_PLAIN}[f[0]], int(f[1]), int(f[2]), int(f[3]),
+                          int(f[4]), ring)
     elif not args.no_tune:
         sa, sb = torch.empty_like(A), torch.empty_like(A)
         tune_glups = J.jacobi_tune(h, sa, sb)
@@ -357,16 +359,24 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fp64_512", choices=sorted(WORKLOADS))
-    ap.add_argument("--plan", default=None, help="force a plan, e.g. tb:4:64:16:64 or plain:1:1:1:1")
+    ap.add_argument("--plan", default=None, help="force a plan kernel:depth:bx:by:bz[:ring], e.g. tb:4:64:16:64:8 or plain:1:1:1:1")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--n", type=int, default=None, help="override the cubic interior size (profiling cases)")
+    ap.add_argument("--T", type=int, default=None, help="override the sweeps per step (profiling cases)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.n is not None:
+        w["n"] = (args.n, args.n, args.n)
+        w["name"] += "_resized_%d" % args.n
+    if args.T is not None:
+        w["T"] = args.T
+        w["name"] += "_T%d" % args.T
     if args.impl == "reference":
         return run_reference(args, w)
     return run_ours(args, w)

@@ -101,8 +101,9 @@ int check_plan(const jacobi_plan_s *h, const Plan &p)
     if (p.kernel == JACOBI_KERNEL_PLAIN) return JACOBI_OK;
     if (p.kernel != JACOBI_KERNEL_TB) return JACOBI_ERR_ARG;
     if (p.depth < 1 || p.depth > 16 || p.bx < 1 || p.by < 1 || p.bz < 1) return JACOBI_ERR_ARG;
+    if (p.ring != 0 && p.ring != 4 && p.ring != 8 && p.ring != 16) return JACOBI_ERR_ARG;
     TbLaunch L;
-    if (tb_configure(h->dtype, p.depth, p.bx, p.by, &L) != cudaSuccess) return JACOBI_ERR_UNSUPPORTED;
+    if (tb_configure(h->dtype, p.depth, p.bx, p.by, p.ring, &L) != cudaSuccess) return JACOBI_ERR_UNSUPPORTED;
     int clusters = 0;
     cudaError_t e = tb_max_clusters(h->dtype, L, p.depth, &clusters);
     if (e != cudaSuccess) {
@@ -153,7 +154,7 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
     int Ldepth = -1;
     for (int q = 0; q < P; ++q) {
         if (depths[q] != Ldepth) {
-            if (tb_configure(h->dtype, depths[q], p.bx, p.by, &L) != cudaSuccess) return JACOBI_ERR_UNSUPPORTED;
+            if (tb_configure(h->dtype, depths[q], p.bx, p.by, p.ring, &L) != cudaSuccess) return JACOBI_ERR_UNSUPPORTED;
             Ldepth = depths[q];
         }
         a.depth = depths[q];
@@ -161,6 +162,7 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
         a.H = L.H;
         a.Wp = L.Wp;
         a.R = L.R;
+        a.rshift = (L.R == 16) ? 4 : (L.R == 8 ? 3 : 2);
         a.src = (q % 2 == 0) ? A : B;
         a.dst = (q % 2 == 0) ? B : A;
         a.fault_mode = h->fault_mode;
@@ -287,7 +289,7 @@ int jacobi_sweep_host(jacobi_h h, const void *A_host, void *out_host, int T, jac
     return JACOBI_OK;
 }
 
-int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz)
+int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, int ring)
 {
     if (!h) return JACOBI_ERR_ARG;
     if (kernel == JACOBI_KERNEL_AUTO) {
@@ -300,6 +302,7 @@ int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz)
     p.bx = bx;
     p.by = by;
     p.bz = bz;
+    p.ring = (kernel == JACOBI_KERNEL_PLAIN) ? 0 : ring;
     const int st = check_plan(h, p);
     if (st != JACOBI_OK) return st;
     h->plan = p;
@@ -307,7 +310,7 @@ int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz)
     return JACOBI_OK;
 }
 
-int jacobi_get_plan(jacobi_h h, int *kernel, int *depth, int *bx, int *by, int *bz)
+int jacobi_get_plan(jacobi_h h, int *kernel, int *depth, int *bx, int *by, int *bz, int *ring)
 {
     if (!h) return JACOBI_ERR_ARG;
     const Plan p = active_plan(h);
@@ -316,6 +319,7 @@ int jacobi_get_plan(jacobi_h h, int *kernel, int *depth, int *bx, int *by, int *
     if (bx) *bx = p.bx;
     if (by) *by = p.by;
     if (bz) *bz = p.bz;
+    if (ring) *ring = p.ring;
     return JACOBI_OK;
 }
 
@@ -375,34 +379,56 @@ int jacobi_profile_read(jacobi_h h, double *pass_ms, int *pass_launches, int *ot
     return JACOBI_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Times plan p (T = 4*depth sweeps, best of two after a warm-up) in GLUP/s.
+int time_plan(jacobi_plan_s *h, const Plan &p, void *A, void *B, cudaStream_t s, cudaEvent_t e0,
+              cudaEvent_t e1, double *glups)
+{
+    const int T = 4 * p.depth;
+    int st = run_sweeps(h, p, A, B, T, s);
+    if (st != JACOBI_OK) return st;
+    float best = 1e30f;
+    for (int r = 0; r < 2; ++r) {
+        cudaEventRecord(e0, s);
+        st = run_sweeps(h, p, A, B, T, s);
+        if (st != JACOBI_OK) return st;
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) return cuda_fail(e);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    *glups = (double)h->nx * h->ny * h->nz * T / (best * 1e-3) / 1e9;
+    return JACOBI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stream, double *glups)
 {
     if (!h || !scratchA || !scratchB || scratchA == scratchB) return JACOBI_ERR_ARG;
     if (!aligned16(scratchA) || !aligned16(scratchB)) return JACOBI_ERR_ALIGN;
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<Plan> cands;
     const bool f64 = h->dtype == JACOBI_F64;
+    // Stage 1: depth x tile with the automatic ring depth and a fixed z chunk.
+    // Stage 2: z chunk and ring depth (pipeline looseness) around the winner.
     const int depths64[] = {1, 2, 4};
     const int depths32[] = {1, 2, 4, 6, 8};
     const int tiles[][2] = {{32, 16}, {64, 8}, {64, 16}, {32, 32}, {64, 32}, {128, 16}, {128, 32}, {64, 64}};
     const int bzs[] = {32, 64, 128, 256};
-    const int *dl = f64 ? depths64 : depths32;
-    const int nd = f64 ? 3 : 5;
-    for (int di = 0; di < nd; ++di)
-        for (const auto &t : tiles)
-            for (int bz : bzs) {
-                Plan p;
-                p.kernel = JACOBI_KERNEL_TB;
-                p.depth = dl[di];
-                p.bx = t[0] < h->nx ? t[0] : h->nx;
-                p.by = t[1] < h->ny ? t[1] : h->ny;
-                p.bz = bz < h->nz ? bz : h->nz;
-                bool dup = false;
-                for (const Plan &c : cands)
-                    dup = dup || (c.depth == p.depth && c.bx == p.bx && c.by == p.by && c.bz == p.bz);
-                if (!dup && check_plan(h, p) == JACOBI_OK) cands.push_back(p);
-            }
-    if (cands.empty()) return JACOBI_ERR_UNSUPPORTED;
+    const int rings[] = {4, 8, 16};
+    auto clampp = [&](Plan p) {
+        if (p.bx > h->nx) p.bx = h->nx;
+        if (p.by > h->ny) p.by = h->ny;
+        if (p.bz > h->nz) p.bz = h->nz;
+        return p;
+    };
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -411,39 +437,44 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
         cudaEventDestroy(e0);
         return cuda_fail(e);
     }
-    const double lups_per_sweep = (double)h->nx * h->ny * h->nz;
     double best = -1.0;
-    Plan bestp = cands[0];
+    Plan bestp;
     int st = JACOBI_OK;
-    for (const Plan &p : cands) {
-        const int T = 2 * p.depth;
-        st = run_sweeps(h, p, scratchA, scratchB, T, s);  // warm-up
-        if (st != JACOBI_OK) break;
-        float ms_best = 1e30f;
-        for (int r = 0; r < 2; ++r) {
-            cudaEventRecord(e0, s);
-            st = run_sweeps(h, p, scratchA, scratchB, T, s);
-            if (st != JACOBI_OK) break;
-            cudaEventRecord(e1, s);
-            e = cudaEventSynchronize(e1);
-            if (e != cudaSuccess) {
-                st = cuda_fail(e);
-                break;
-            }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < ms_best) ms_best = ms;
-        }
-        if (st != JACOBI_OK) break;
-        const double g = lups_per_sweep * T / (ms_best * 1e-3) / 1e9;
-        if (g > best) {
+    auto consider = [&](const Plan &p) {
+        if (st != JACOBI_OK || check_plan(h, p) != JACOBI_OK) return;
+        double g = 0.0;
+        st = time_plan(h, p, scratchA, scratchB, s, e0, e1, &g);
+        if (st == JACOBI_OK && g > best) {
             best = g;
             bestp = p;
         }
+    };
+    const int *dl = f64 ? depths64 : depths32;
+    const int nd = f64 ? 3 : 5;
+    for (int di = 0; di < nd; ++di)
+        for (const auto &t : tiles) {
+            Plan p;
+            p.depth = dl[di];
+            p.bx = t[0];
+            p.by = t[1];
+            p.bz = 128;
+            p.ring = 0;
+            consider(clampp(p));
+        }
+    if (st == JACOBI_OK && best > 0) {
+        const Plan base = bestp;
+        for (int bz : bzs)
+            for (int rg : rings) {
+                Plan p = base;
+                p.bz = bz;
+                p.ring = rg;
+                consider(clampp(p));
+            }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != JACOBI_OK) return st;
+    if (best <= 0) return JACOBI_ERR_UNSUPPORTED;
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune_cache[std::make_tuple(h->dtype, h->nx, h->ny, h->nz, h->sms)] = bestp;

@@ -4,7 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/jacobi.h"
+#include "jacobi.h"
 
 namespace jac {
 
@@ -17,7 +17,8 @@ struct TbArgs {
     int bx, by, bz;     // tile interior (x, y) and z chunk (interior planes)
     int ntx;            // number of x tiles (grid.x = D * ntx)
     int W, H, Wp;       // ring plane: width bx+2D, height by+2D, padded pitch
-    int R;              // ring slots per CTA
+    int R;              // ring slots per CTA (power of two, <= 16)
+    int rshift;         // log2(R)
     int *status;        // device status word (first error code wins)
     unsigned long long limit_ns;  // bound of every device-side wait
     int fault_mode;     // test hook: 1 = drop one arrival (see jacobi.h)
@@ -35,6 +36,7 @@ struct Plan {
     int kernel = JACOBI_KERNEL_TB;
     int depth = 1;
     int bx = 64, by = 16, bz = 64;
+    int ring = 0;  // ring slots per CTA (4, 8, 16); 0 = largest that fits the budget
 };
 
 // Launch resources of a TB plan (host side), filled by tb_configure.
@@ -45,10 +47,9 @@ struct TbLaunch {
     int W = 0, H = 0, Wp = 0;
 };
 
-constexpr int kTbThreadsLoader = 32;
 
 // Kernels (sweep_kernels.cu).  All return cudaError_t of the launch.
-cudaError_t tb_configure(int dtype, int depth, int bx, int by, TbLaunch *out);
+cudaError_t tb_configure(int dtype, int depth, int bx, int by, int ring, TbLaunch *out);
 cudaError_t tb_launch(int dtype, const TbArgs &a, const TbLaunch &L, cudaStream_t s);
 cudaError_t tb_max_clusters(int dtype, const TbLaunch &L, int depth, int *clusters);
 cudaError_t plain_launch(int dtype, const PlainArgs &a, cudaStream_t s);

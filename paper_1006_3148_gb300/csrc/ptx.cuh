@@ -51,7 +51,7 @@ __device__ __forceinline__ bool mbar_try_wait_parity(uint32_t bar, uint32_t pari
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(bar), "r"(parity)
@@ -59,20 +59,23 @@ __device__ __forceinline__ bool mbar_try_wait_parity(uint32_t bar, uint32_t pari
     return ok != 0;
 }
 
-// Arrive on a barrier of this CTA.
+// Arrivals that only signal "this slot was read": the reads they follow
+// have completed (their values were consumed), so no memory ordering is
+// requested.  A release arrive would instead wait for every earlier global
+// store of the thread to drain, which costs thousands of cycles per plane.
 __device__ __forceinline__ void mbar_arrive_local(uint32_t bar)
 {
     asm volatile(
         "{\n\t.reg .b64 st;\n\t"
-        "mbarrier.arrive.release.cluster.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
+        "mbarrier.arrive.relaxed.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
         : "memory");
 }
 
-// Arrive on a barrier given by a shared::cluster address (any CTA of the
-// cluster, including this one).
+// Same, on a barrier given by a shared::cluster address (any CTA of the
+// cluster).
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar)
 {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar)
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar)
                  : "memory");
 }
 
@@ -100,6 +103,44 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, float v)
     asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
+// 16-byte store of a group to another CTA's shared memory.  No "memory"
+// clobber: ordering against the consumer is established by the barrier and
+// the release-arrive that follow, which are themselves ordered asm.
+__device__ __forceinline__ void st_cluster_v(uint32_t addr, const float (&v)[4])
+{
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+                 "f"(v[3]));
+}
+__device__ __forceinline__ void st_cluster_v(uint32_t addr, const double (&v)[2])
+{
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(addr), "d"(v[0]), "d"(v[1]));
+}
+
+// Asynchronous 16-byte store into another CTA's shared memory whose byte
+// count completes on that CTA's mbarrier (addresses are shared::cluster).
+__device__ __forceinline__ void st_async_v(uint32_t addr, const float (&v)[4], uint32_t mbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+                 "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async_v(uint32_t addr, const double (&v)[2], uint32_t mbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(addr),
+                 "d"(v[0]), "d"(v[1]), "r"(mbar)
+                 : "memory");
+}
+
+// Arrival on a barrier of this CTA that also raises its expected byte count.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.relaxed.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+        "r"(bytes)
+        : "memory");
+}
+
 __device__ __forceinline__ void fence_acq_rel_cluster()
 {
     asm volatile("fence.acq_rel.cluster;" ::: "memory");
@@ -116,7 +157,34 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
         : "memory");
 }
 
-// Wait for completion of the barrier phase with the given parity.  Gives up
+// Element-wise asynchronous copy global -> shared (4 or 8 bytes, naturally
+// aligned), and an arrival on `bar` once all of this thread's earlier
+// cp.async operations have completed (the arrival does not raise the
+// pending count: the barrier's expected count includes these arrivals).
+__device__ __forceinline__ void cp_async_4(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Wait for completion of the barrier phase with the given parity (acquire at
+// CTA scope: data that completed the phase through cp.async or st.async
+// transaction counts is visible to the waiting thread afterwards).  Gives up
 // (returns false) once `limit_ns` has passed, or early when `abort_flag`
 // (if not null) becomes nonzero.  Never traps.
 __device__ __forceinline__ bool wait_parity_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns,

@@ -91,25 +91,70 @@ __global__ void __launch_bounds__(256) plain_pass_kernel(const PlainArgs a)
 }
 
 // -------------------------------------------------------- time-skewed pass
-// Thread roles: threads [0, NC) compute (each owns up to MAXC cells of the
-// level's output region, fixed for the whole z stream, with a register queue
-// of the values at planes k-1 and k); warp NC/32 of the level-1 CTA issues
-// the bulk copies that stream input planes from HBM into its ring.
+// Cells are handled in groups of VEC = 16/sizeof(T) consecutive x cells of
+// one row (4 FP32 / 2 FP64), aligned so that a group starts at a global x
+// that is a multiple of VEC.  Every thread owns up to MAXG groups of its
+// level's output region, fixed for the whole z stream, and keeps per group
+// the values at planes k-1 and k of its input level in registers (the z
+// queue).  One step (output plane k) reads, per group, the rows y-1 and y+1
+// of plane k and the group of plane k+1 with 16-byte shared loads, plus the
+// two x-neighbours at the group's ends.
 //
-// Shared memory of every CTA: ring[R][H][Wp] of T (slot = one z-plane of
-// the tile widened by D cells), then three arrays of R mbarriers:
-//   in_full[s]   slot s holds its plane (level 1: byte count of the bulk
-//                copies; level >= 2: one arrival from the producer CTA)
-//   in_empty[s]  level 1 only: its compute threads released slot s
-//   out_empty[s] the next CTA released its slot s (remote arrival)
-// Element (x, y) of a slot sits at column (x - (x0-D)) + off, row y-(y0-D).
-// off = 0 except in level 1's ring, whose rows are copied whole 16-byte
-// units from global memory: there off = (global row start misalignment)/s.
-template <typename T, int NC, int MAXC>
-__global__ void __launch_bounds__(NC + kTbThreadsLoader, 1) tb_pass_kernel(const TbArgs a)
+// Shared memory of every CTA: ring[R][H][Wp] of T.  Slot = one z-plane of
+// the tile widened by D cells; element (x, y) sits at column x - xs and row
+// y - (y0 - D), where xs is a multiple of VEC at least one group left of
+// x0 - D (so every group's left neighbour is inside its row).  Then three
+// arrays of R mbarriers:
+//   in_full[s]   slot s holds its plane.  Level 1 streams its input from
+//                global memory itself: each thread issues cp.async copies
+//                for plane n+R-2 while computing plane n and arrives (on
+//                completion of its copies) once per plane: expected count
+//                NC.  Level >= 2: the producer CTA writes the plane with
+//                st.async, each store completing its bytes on this barrier;
+//                the barrier is armed with the plane's byte count (one
+//                arrival) by warp 0 before the slot is released.
+//   in_empty[s]  level 1: every warp released slot s (count NC/32), waited
+//                on before copying the next plane into the slot.
+//   out_empty[s] level < D: every warp of the next CTA released its slot s
+//                (count NC/32, remote arrivals).
+// No CTA-wide barrier runs per plane: warps advance independently, held
+// together only by these slot barriers (the relaxed synchronisation of
+// Sect. 2.2: a consumer waits for its producer to be one plane ahead, a
+// producer waits until its consumer freed the slot, R planes of looseness).
+//
+// Lanes of a group outside this level's region or outside the grid compute
+// values nobody reads; lanes on the grid's halo keep their own value.
+__host__ __device__ __forceinline__ int floor_div(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
+
+template <typename T>
+struct VecOf;
+template <>
+struct VecOf<float> {
+    using V = float4;
+};
+template <>
+struct VecOf<double> {
+    using V = double2;
+};
+
+// Groups (VEC-aligned) covering [xa, xb) x [ya, yb): count per row and rows.
+__device__ __forceinline__ void region_groups(int xa, int xb, int ya, int yb, int xs, int vec, int *jg0,
+                                              int *gpr, int *rows)
+{
+    *jg0 = floor_div(xa - xs, vec);
+    *gpr = floor_div(xb - xs + vec - 1, vec) - *jg0;
+    *rows = yb - ya;
+}
+
+template <typename T, int NC, int MAXG, int MAXLD>
+__global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_pass_kernel(const TbArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int V = 16 / (int)sizeof(T);
+    constexpr int VEC = 16 / (int)sizeof(T);
+    constexpr int NW = NC / 32;
+    using V = typename VecOf<T>::V;
+    const int R = a.R, rsh = a.rshift, rmask = a.R - 1;
+    const int L = R - 2;  // level-1 load lookahead (planes)
     const int D = a.depth;
     const int rank = (int)cluster_ctarank();
     const int lvl = rank + 1;
@@ -118,194 +163,272 @@ __global__ void __launch_bounds__(NC + kTbThreadsLoader, 1) tb_pass_kernel(const
     const int x0 = 1 + (int)(blockIdx.x / D) * a.bx, x1 = min(x0 + a.bx, nx + 1);
     const int y0 = 1 + (int)blockIdx.y * a.by, y1 = min(y0 + a.by, ny + 1);
     const int z0 = 1 + (int)blockIdx.z * a.bz, z1 = min(z0 + a.bz, nz + 1);
-    const int gx = x0 - D, gy = y0 - D;
-    const int Wp = a.Wp, R = a.R;
+    const int xs = VEC * floor_div(x0 - D, VEC) - VEC;  // global x of shared column 0
+    const int ys = y0 - D;                              // global y of shared row 0
+    const int Wp = a.Wp;
     const int slot_elems = a.H * Wp;
     T *ring = reinterpret_cast<T *>(smem);
     const uint32_t ring_s = smem_addr(ring);
-    const uint32_t in_full = ring_s + (uint32_t)(R * slot_elems * (int)sizeof(T));
+    const uint32_t slot_bytes = (uint32_t)(slot_elems * (int)sizeof(T));
+    const uint32_t in_full = ring_s + (uint32_t)R * slot_bytes;
     const uint32_t in_empty = in_full + 8u * R;
     const uint32_t out_empty = in_full + 16u * R;
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const volatile int *vstatus = a.status;
-
-    if (tid == 0) {
-        for (int s = 0; s < R; ++s) {
-            mbar_init(in_full + 8u * s, 1);
-            mbar_init(in_empty + 8u * s, 1);
-            mbar_init(out_empty + 8u * s, 1);
-        }
-        fence_mbar_init_cluster();
-    }
-    cluster_sync_all();
+    const long long plane = (long long)NYP * NXP;
 
     const int wl = D - lvl;  // this level's region is the tile widened by wl
     const int zo0 = max(z0 - wl, 0), zo1 = min(z1 + wl, nz + 2);
     const int zi0 = max(z0 - wl - 1, 0), zi1 = min(z1 + wl + 1, nz + 2);
+    const int nin = zi1 - zi0;
 
-    if (tid >= NC) {
-        // ------------------------------------------------ level-1 loader warp
-        if (lvl == 1) {
-            const int lane = tid - NC;
-            const int ix0 = max(gx, 0), ix1 = min(x1 + D, NXP);
-            const int iy0 = max(gy, 0), iy1 = min(y1 + D, NYP);
-            const char *src = static_cast<const char *>(a.src);
-            const long long es = sizeof(T);
-            int n_issued = 0;
-            for (int n = 0; n < zi1 - zi0; ++n) {
-                const int k = zi0 + n, s = n % R;
-                int ok = (*vstatus == 0);
-                if (ok && n >= R && lane == 0)
-                    ok = wait_parity_bounded(in_empty + 8u * s, ((n / R) - 1) & 1, a.limit_ns, vstatus);
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) {
-                    if (lane == 0) record_error(a.status, JACOBI_ERR_TIMEOUT);
-                    break;
-                }
-                // Halo planes only feed z-neighbours of interior cells: rows 1..ny.
-                const bool hz = (k == 0 || k == nz + 1);
-                const int jr0 = hz ? max(iy0, 1) : iy0;
-                const int jr1 = hz ? min(iy1, ny + 1) : iy1;
-                uint32_t my_bytes = 0;
-                for (int j = jr0 + lane; j < jr1; j += 32) {
-                    const long long row = ((long long)k * NYP + j) * NXP;
-                    const long long gs = ((row + ix0) * es) & ~15ll;
-                    const long long ge = ((row + ix1) * es + 15) & ~15ll;
-                    my_bytes += (uint32_t)(ge - gs);
-                }
-                if (my_bytes) mbar_expect_tx(in_full + 8u * s, my_bytes);
-                __syncwarp();
-                if (lane == 0 && !(a.fault_mode == 1 && n == 2)) mbar_arrive_local(in_full + 8u * s);
-                for (int j = jr0 + lane; j < jr1; j += 32) {
-                    const long long row = ((long long)k * NYP + j) * NXP;
-                    const long long gs = ((row + ix0) * es) & ~15ll;
-                    const long long ge = ((row + ix1) * es + 15) & ~15ll;
-                    const long long vb = (row + gx) * es;
-                    const long long vs = vb - (((vb % 16) + 16) % 16);  // floor to 16 bytes
-                    const uint32_t dst = ring_s + (uint32_t)((s * slot_elems + (j - gy) * Wp) * (int)es) +
-                                         (uint32_t)(gs - vs);
-                    bulk_g2s(dst, src + gs, (uint32_t)(ge - gs), in_full + 8u * s);
-                }
-                n_issued = n + 1;
-            }
-            // Never leave with copies in flight into this CTA's shared memory.
-            if (lane == 0)
-                for (int n = max(0, n_issued - R); n < n_issued; ++n)
-                    wait_parity_bounded(in_full + 8u * (n % R), (n / R) & 1, a.limit_ns, nullptr);
-            __syncwarp();
-        }
-    } else {
-        // ---------------------------------------------------- compute threads
-        const int ox0 = max(x0 - wl, 0), ox1 = min(x1 + wl, NXP);
-        const int oy0 = max(y0 - wl, 0), oy1 = min(y1 + wl, NYP);
-        const int Wo = ox1 - ox0, Ho = oy1 - oy0, ncell = Wo * Ho;
-        const int vmask = (lvl == 1) ? V - 1 : 0;
-        const int NXV = NXP & (V - 1);
-        const int PSV = (int)(((long long)NYP * NXP) & (V - 1));
-        const int gxv = gx & (V - 1);
-
-        int lofs[MAXC], yv[MAXC], gofs[MAXC];
-        uint32_t valid = 0, comp = 0;
-#pragma unroll
-        for (int q = 0; q < MAXC; ++q) {
-            const int idx = tid + q * NC;
-            const int x = ox0 + (idx % Wo), y = oy0 + (idx / Wo);
-            lofs[q] = (y - gy) * Wp + (x - gx);
-            yv[q] = (y * NXV) & (V - 1);
-            gofs[q] = y * NXP + x;
-            if (idx < ncell) valid |= 1u << q;
-            if (idx < ncell && x >= 1 && x <= nx && y >= 1 && y <= ny) comp |= 1u << q;
-        }
-
-        const uint32_t next_ring = (lvl < D) ? mapa(ring_s, rank + 1) : 0u;
-        const uint32_t next_full = (lvl < D) ? mapa(in_full, rank + 1) : 0u;
-        const uint32_t prev_oe = (lvl > 1) ? mapa(out_empty, rank - 1) : 0u;
-        T *dst = static_cast<T *>(a.dst);
-        const long long plane = (long long)NYP * NXP;
-        bool dead = false;
-        auto wait = [&](uint32_t bar, int parity) {
-            if (dead) return;
-            if (!wait_parity_bounded(bar, (uint32_t)parity, a.limit_ns, vstatus)) {
-                dead = true;
-                record_error(a.status, JACOBI_ERR_TIMEOUT);
-            }
-        };
-        auto release = [&](int seq) {
-            const uint32_t off = 8u * (uint32_t)(seq % R);
-            if (lvl == 1) mbar_arrive_local(in_empty + off);
-            else mbar_arrive_cluster(prev_oe + off);
-        };
-        auto own = [&](int p, int q) -> T {
-            const int n = p - zi0;
-            const int ok = (p * PSV + gxv + yv[q]) & vmask;
-            return ring[(n % R) * slot_elems + lofs[q] + ok];
-        };
-
-        T av[MAXC], bv[MAXC];
-#pragma unroll
-        for (int q = 0; q < MAXC; ++q) av[q] = bv[q] = T(0);
-        if (zo0 > zi0) {
-            wait(in_full, 0);
-#pragma unroll
-            for (int q = 0; q < MAXC; ++q)
-                if (valid & (1u << q)) av[q] = own(zo0 - 1, q);
-        }
-        {
-            const int n = zo0 - zi0;
-            wait(in_full + 8u * (n % R), (n / R) & 1);
-#pragma unroll
-            for (int q = 0; q < MAXC; ++q)
-                if (valid & (1u << q)) bv[q] = own(zo0, q);
-        }
-
-        for (int k = zo0; k < zo1; ++k) {
-            const int n = k - zi0, m = k - zo0;
-            const bool has_next = (k + 1 < zi1);
-            const bool interior_k = (k >= 1 && k <= nz);
-            T cv[MAXC];
-#pragma unroll
-            for (int q = 0; q < MAXC; ++q) cv[q] = T(0);
-            if (has_next) {
-                wait(in_full + 8u * ((n + 1) % R), ((n + 1) / R) & 1);
-#pragma unroll
-                for (int q = 0; q < MAXC; ++q)
-                    if (valid & (1u << q)) cv[q] = own(k + 1, q);
-            }
-            if (lvl < D && m >= R) wait(out_empty + 8u * (m % R), ((m / R) - 1) & 1);
-
-            const T *cen = ring + (n % R) * slot_elems;
-            const int okc = (k * PSV + gxv) & vmask;
-#pragma unroll
-            for (int q = 0; q < MAXC; ++q) {
-                if (!(valid & (1u << q))) continue;
-                T v = bv[q];
-                if (interior_k && (comp & (1u << q))) {
-                    const int oc = (okc + yv[q]) & vmask;
-                    const int c = lofs[q] + oc;
-                    const T wv = cen[c - 1];
-                    const T ev = cen[c + 1];
-                    const T sv = cen[lofs[q] - Wp + ((okc + yv[q] - NXV) & vmask)];
-                    const T nv = cen[lofs[q] + Wp + ((okc + yv[q] + NXV) & vmask)];
-                    v = Arith<T>::update(wv, ev, sv, nv, av[q], cv[q]);
-                }
-                if (lvl < D)
-                    st_cluster(next_ring + (uint32_t)(((m % R) * slot_elems + lofs[q]) * (int)sizeof(T)), v);
-                else
-                    dst[k * plane + gofs[q]] = v;
-                av[q] = bv[q];
-                bv[q] = cv[q];
-            }
-            named_bar_sync(1, NC);
-            if (tid == 0) {
-                if (lvl < D) {
-                    fence_acq_rel_cluster();
-                    mbar_arrive_cluster(next_full + 8u * (uint32_t)(m % R));
-                }
-                if (k == zo0 && zo0 > zi0) release(n - 1);
-                release(n);
-            }
-        }
+    // bytes of one input plane written by the producer level (its groups)
+    uint32_t in_bytes = 0;
+    if (lvl > 1) {
+        int jg, gp, rows;
+        region_groups(max(x0 - wl - 1, 0), min(x1 + wl + 1, NXP), max(y0 - wl - 1, 0), min(y1 + wl + 1, NYP), xs, VEC,
+                      &jg, &gp, &rows);
+        in_bytes = (uint32_t)(gp * rows) * 16u;
     }
+    if (tid == 0) {
+        for (int s = 0; s < R; ++s) {
+            mbar_init(in_full + 8u * s, lvl == 1 ? NC : 1);
+            mbar_init(in_empty + 8u * s, NW);
+            mbar_init(out_empty + 8u * s, NW);
+        }
+        fence_mbar_init_cluster();
+        if (lvl > 1)
+            for (int s = 0; s < R && s < nin; ++s) mbar_arrive_expect_tx(in_full + 8u * s, in_bytes);
+    }
+    cluster_sync_all();
+
+    bool dead = false;
+    auto wait = [&](uint32_t bar, int parity) {
+        if (dead) return;
+        if (!wait_parity_bounded(bar, (uint32_t)parity, a.limit_ns, vstatus)) {
+            dead = true;
+            record_error(a.status, JACOBI_ERR_TIMEOUT);
+        }
+    };
+
+    // ---- level-1 input streaming.  Every row is copied in pieces of cs
+    // elements, cs = the largest of VEC, 2, 1 that divides the row pitch, so
+    // that a piece is naturally aligned in global memory in every row and
+    // plane (the base pointer is 16-byte aligned); elements left of the first
+    // or right of the last full piece of a row are copied one by one.  Every
+    // row has the same piece layout, so each thread precomputes its pieces
+    // (row and column inside the tile, size) once, packed in one register,
+    // and re-issues them for every plane.
+    const T *src = static_cast<const T *>(a.src);
+    const int ix0 = max(x0 - D, 0), ix1 = min(x1 + D, NXP);
+    const int iy0 = max(ys, 0), iy1 = min(y1 + D, NYP);
+    const int cs = (NXP % VEC == 0) ? VEC : ((VEC == 4 && NXP % 2 == 0) ? 2 : 1);
+    const int cxa = ((ix0 + cs - 1) / cs) * cs, cxb = (ix1 / cs) * cs;
+    const int nl = (cxb > cxa) ? cxa - ix0 : ix1 - ix0;  // single elements on the left
+    const int nf = (cxb > cxa) ? (cxb - cxa) / cs : 0;    // full pieces
+    const int nr = (cxb > cxa) ? ix1 - cxb : 0;           // single elements on the right
+    const int ppr = nl + nf + nr, npieces = ppr * (iy1 - iy0);
+    uint32_t piece[MAXLD];  // bits 0..11 column - xs, 12..27 row - ys, 28..29 log2(bytes) - 2
+    const bool use_pieces = (lvl == 1) && npieces <= NC * MAXLD;
+#pragma unroll
+    for (int q = 0; q < MAXLD; ++q) {
+        const int i = tid + q * NC;
+        uint32_t pc = 0xffffffffu;
+        if (use_pieces && i < npieces) {
+            const int r = i / ppr, pi = i % ppr;
+            int x, bytes = (int)sizeof(T);
+            if (pi < nl) x = ix0 + pi;
+            else if (pi < nl + nf) {
+                x = cxa + (pi - nl) * cs;
+                bytes = cs * (int)sizeof(T);
+            } else x = cxb + (pi - nl - nf);
+            const int lg = (bytes == 16) ? 2 : (bytes == 8 ? 1 : 0);
+            pc = (uint32_t)(x - xs) | ((uint32_t)(iy0 + r - ys) << 12) | ((uint32_t)lg << 28);
+        }
+        piece[q] = pc;
+    }
+    int issued = 0;
+    auto issue_upto = [&](int last) {
+        if (lvl != 1) return;
+        for (; issued <= last && issued < nin; ++issued) {
+            const int n = issued, slot = n & rmask;
+            if (n >= R) wait(in_empty + 8u * slot, ((n >> rsh) - 1) & 1);
+            const T *gp = src + (long long)(zi0 + n) * plane + (long long)ys * NXP + xs;
+            const uint32_t sb = ring_s + (uint32_t)slot * slot_bytes;
+            if (use_pieces) {
+#pragma unroll
+                for (int q = 0; q < MAXLD; ++q) {
+                    const uint32_t pc = piece[q];
+                    if (pc == 0xffffffffu) continue;
+                    const int xl = (int)(pc & 0xfffu), yl = (int)((pc >> 12) & 0xffffu);
+                    const uint32_t d = sb + (uint32_t)((yl * Wp + xl) * (int)sizeof(T));
+                    const T *g = gp + (yl * NXP + xl);
+                    const uint32_t lg = pc >> 28;
+                    if (lg == 2) cp_async_16(d, g);
+                    else if (lg == 1) cp_async_8(d, g);
+                    else cp_async_4(d, g);
+                }
+            } else {
+                // general layout: warp w copies rows w, w+NC/32, ... one element per lane
+                for (int y = iy0 + warp; y < iy1; y += NW) {
+                    const T *grow = gp + (long long)(y - ys) * NXP - xs;
+                    const uint32_t srow = sb + (uint32_t)(((y - ys) * Wp - xs) * (int)sizeof(T));
+                    for (int x = ix0 + lane; x < ix1; x += 32) {
+                        if (sizeof(T) == 8) cp_async_8(srow + (uint32_t)x * 8u, grow + x);
+                        else cp_async_4(srow + (uint32_t)x * 4u, grow + x);
+                    }
+                }
+            }
+            if (!(a.fault_mode == 1 && n == 2 && tid == 0)) cp_async_arrive_noinc(in_full + 8u * slot);
+        }
+    };
+    issue_upto(L - 1);
+
+    // ---- groups of this thread
+    int jg0, gpr, orows;
+    const int ox0 = max(x0 - wl, 0), ox1 = min(x1 + wl, NXP);
+    const int oy0 = max(y0 - wl, 0), oy1 = min(y1 + wl, NYP);
+    region_groups(ox0, ox1, oy0, oy1, xs, VEC, &jg0, &gpr, &orows);
+    const int ngroups = gpr * orows;
+    int goff[MAXG], gofs[MAXG];
+    uint32_t flags[MAXG];  // bit 0 valid, bit 1 row interior, bits 2.. interior lanes, bits 8.. store lanes
+#pragma unroll
+    for (int q = 0; q < MAXG; ++q) {
+        const int g = tid + q * NC;
+        const int j = jg0 + (g % gpr), y = oy0 + g / gpr;
+        const int xg = xs + VEC * j;
+        goff[q] = (y - ys) * Wp + VEC * j;
+        gofs[q] = y * NXP + xg;
+        uint32_t f = 0;
+        if (g < ngroups) {
+            f |= 1u;
+            if (y >= 1 && y <= ny) f |= 2u;
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) {
+                const int x = xg + l;
+                if (x >= 1 && x <= nx) f |= 4u << l;
+                if (x >= x0 && x < x1) f |= 256u << l;
+            }
+        }
+        flags[q] = f;
+    }
+
+    const uint32_t next_ring = (lvl < D) ? mapa(ring_s, rank + 1) : 0u;
+    const uint32_t next_full = (lvl < D) ? mapa(in_full, rank + 1) : 0u;
+    const uint32_t prev_oe = (lvl > 1) ? mapa(out_empty, rank - 1) : 0u;
+    T *dst = static_cast<T *>(a.dst);
+    // Release of input seq by this warp (after its last read of the slot).
+    // Warp 0 first re-arms the slot for the seq that will follow in it.
+    auto release = [&](int seq) {
+        __syncwarp();
+        if (lane != 0) return;
+        const uint32_t off = 8u * (uint32_t)(seq & rmask);
+        if (lvl == 1) {
+            mbar_arrive_local(in_empty + off);
+        } else {
+            if (warp == 0 && seq + R < nin) mbar_arrive_expect_tx(in_full + off, in_bytes);
+            mbar_arrive_cluster(prev_oe + off);
+        }
+    };
+    auto ldv = [&](const T *p, T (&v)[VEC]) {
+        const V t = *reinterpret_cast<const V *>(p);
+        if constexpr (VEC == 4) {
+            v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else {
+            v[0] = t.x; v[1] = t.y;
+        }
+    };
+
+    T av[MAXG][VEC], bv[MAXG][VEC];
+#pragma unroll
+    for (int q = 0; q < MAXG; ++q)
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) av[q][l] = bv[q][l] = T(0);
+    if (zo0 > zi0) {
+        wait(in_full, 0);
+#pragma unroll
+        for (int q = 0; q < MAXG; ++q)
+            if (flags[q] & 1u) ldv(ring + goff[q], av[q]);
+    }
+    {
+        const int n = zo0 - zi0;
+        wait(in_full + 8u * (n & rmask), (n >> rsh) & 1);
+        const T *pl = ring + (n & rmask) * slot_elems;
+#pragma unroll
+        for (int q = 0; q < MAXG; ++q)
+            if (flags[q] & 1u) ldv(pl + goff[q], bv[q]);
+    }
+
+    for (int k = zo0; k < zo1; ++k) {
+        const int n = k - zi0, m = k - zo0;
+        issue_upto(n + L);
+        const bool has_next = (k + 1 < zi1);
+        const bool interior_k = (k >= 1 && k <= nz);
+        T cv[MAXG][VEC];
+#pragma unroll
+        for (int q = 0; q < MAXG; ++q)
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) cv[q][l] = T(0);
+        if (has_next) {
+            wait(in_full + 8u * ((n + 1) & rmask), ((n + 1) >> rsh) & 1);
+            const T *pl = ring + ((n + 1) & rmask) * slot_elems;
+#pragma unroll
+            for (int q = 0; q < MAXG; ++q)
+                if (flags[q] & 1u) ldv(pl + goff[q], cv[q]);
+        }
+        if (lvl < D && m >= R) wait(out_empty + 8u * (m & rmask), ((m >> rsh) - 1) & 1);
+
+        const T *cen = ring + (n & rmask) * slot_elems;
+        const uint32_t out_base = next_ring + (uint32_t)(m & rmask) * slot_bytes;
+        const uint32_t out_bar = next_full + 8u * (uint32_t)(m & rmask);
+        T *drow = dst + k * plane;
+#pragma unroll
+        for (int q = 0; q < MAXG; ++q) {
+            const uint32_t f = flags[q];
+            if (!(f & 1u)) continue;
+            T v[VEC];
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) v[l] = bv[q][l];
+            if (interior_k && (f & 2u)) {
+                const T *c = cen + goff[q];
+                T sv[VEC], nv[VEC];
+                ldv(c - Wp, sv);
+                ldv(c + Wp, nv);
+                const T wv = c[-1], ev = c[VEC];
+#pragma unroll
+                for (int l = 0; l < VEC; ++l) {
+                    const T left = (l == 0) ? wv : bv[q][l - 1];
+                    const T right = (l == VEC - 1) ? ev : bv[q][l + 1];
+                    const T u = Arith<T>::update(left, right, sv[l], nv[l], av[q][l], cv[q][l]);
+                    if (f & (4u << l)) v[l] = u;
+                }
+            }
+            if (lvl < D) {
+                st_async_v(out_base + (uint32_t)goff[q] * (uint32_t)sizeof(T), v, out_bar);
+            } else {
+                T *gpo = drow + gofs[q];
+                if ((f & (((1u << VEC) - 1u) << 8)) == (((1u << VEC) - 1u) << 8) && cs == VEC) {
+                    V t;
+                    if constexpr (VEC == 4) t = make_float4(v[0], v[1], v[2], v[3]);
+                    else t = make_double2(v[0], v[1]);
+                    *reinterpret_cast<V *>(gpo) = t;
+                } else {
+#pragma unroll
+                    for (int l = 0; l < VEC; ++l)
+                        if (f & (256u << l)) gpo[l] = v[l];
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) {
+                av[q][l] = bv[q][l];
+                bv[q][l] = cv[q][l];
+            }
+        }
+        if (k == zo0 && zo0 > zi0) release(n - 1);
+        release(n);
+    }
+    cp_async_wait_all();
     cluster_sync_all();
 }
 
@@ -315,18 +438,27 @@ namespace {
 struct Variant {
     int nc, maxc;
 };
-constexpr Variant kVariants[] = {{128, 2}, {128, 4}, {256, 4}, {256, 8}, {512, 8}, {512, 16}};
+constexpr size_t kRingBudget = 100 * 1024;  // auto ring depth: fit 2 CTAs per SM
+// Preferred order: the widest CTA whose threads cover the level-1 groups
+// (more warps per SM hide the latency of the per-plane pipeline).
+constexpr Variant kVariants[] = {{512, 1}, {512, 2}, {256, 2}, {256, 4}, {128, 8}, {256, 6}, {128, 4}, {128, 2}, {128, 6}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kSmemMax = 232448;  // 227 KB per CTA on sm_100-class GPUs
 
+// Load pieces per thread: enough for the level-1 plane of the largest tiles
+// the tuner tries at each thread count (16 = 2048 pieces at 128 threads).
 template <typename T>
-const void *tb_kernel_ptr(int nc, int maxc)
+const void *tb_kernel_ptr(int nc, int maxg)
 {
-    if (nc == 128 && maxc == 2) return (const void *)tb_pass_kernel<T, 128, 2>;
-    if (nc == 128 && maxc == 4) return (const void *)tb_pass_kernel<T, 128, 4>;
-    if (nc == 256 && maxc == 4) return (const void *)tb_pass_kernel<T, 256, 4>;
-    if (nc == 256 && maxc == 8) return (const void *)tb_pass_kernel<T, 256, 8>;
-    if (nc == 512 && maxc == 8) return (const void *)tb_pass_kernel<T, 512, 8>;
-    if (nc == 512 && maxc == 16) return (const void *)tb_pass_kernel<T, 512, 16>;
+    if (nc == 512 && maxg == 1) return (const void *)tb_pass_kernel<T, 512, 1, 4>;
+    if (nc == 512 && maxg == 2) return (const void *)tb_pass_kernel<T, 512, 2, 4>;
+    if (nc == 128 && maxg == 2) return (const void *)tb_pass_kernel<T, 128, 2, 16>;
+    if (nc == 128 && maxg == 4) return (const void *)tb_pass_kernel<T, 128, 4, 16>;
+    if (nc == 128 && maxg == 6) return (const void *)tb_pass_kernel<T, 128, 6, 16>;
+    if (nc == 128 && maxg == 8) return (const void *)tb_pass_kernel<T, 128, 8, 16>;
+    if (nc == 256 && maxg == 2) return (const void *)tb_pass_kernel<T, 256, 2, 8>;
+    if (nc == 256 && maxg == 4) return (const void *)tb_pass_kernel<T, 256, 4, 8>;
+    if (nc == 256 && maxg == 6) return (const void *)tb_pass_kernel<T, 256, 6, 8>;
     return nullptr;
 }
 
@@ -339,25 +471,38 @@ cudaError_t prepare(const void *fn)
 {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 }  // namespace
 
-cudaError_t tb_configure(int dtype, int depth, int bx, int by, TbLaunch *out)
+cudaError_t tb_configure(int dtype, int depth, int bx, int by, int ring, TbLaunch *out)
 {
     const int es = dtype == JACOBI_F64 ? 8 : 4;
     const int V = 16 / es;
     TbLaunch L;
-    L.R = 4;
     L.W = bx + 2 * depth;
     L.H = by + 2 * depth;
-    L.Wp = ((L.W + 2 * V + V - 1) / V) * V;
-    L.smem = (size_t)L.R * L.H * L.Wp * es + 3 * 8 * (size_t)L.R;
-    const long long cells = (long long)(bx + 2 * (depth - 1)) * (by + 2 * (depth - 1));
+    // columns from xs (a group left of x0-D, rounded down to VEC) to the right
+    // neighbour of the last group of x1+D
+    L.Wp = V * ((bx + 2 * depth + 3 * V + V - 1) / V);
+    const size_t slot = (size_t)L.H * L.Wp * es;
+    if (ring == 0) {
+        ring = 4;
+        if (16 * slot <= kRingBudget) ring = 16;
+        else if (8 * slot <= kRingBudget) ring = 8;
+    }
+    if (ring != 4 && ring != 8 && ring != 16) return cudaErrorInvalidValue;
+    L.R = ring;
+    L.smem = (size_t)L.R * slot + 3 * 8 * (size_t)L.R;
+    // groups of the widest output region (level 1): one extra group for the
+    // alignment of its first column
+    const long long groups = (long long)((bx + 2 * (depth - 1) + V - 1) / V + 1) * (by + 2 * (depth - 1));
     L.nc = 0;
     for (const Variant &v : kVariants)
-        if ((long long)v.nc * v.maxc >= cells) {
+        if ((long long)v.nc * v.maxc >= groups) {
             L.nc = v.nc;
             L.maxc = v.maxc;
             break;
@@ -371,7 +516,7 @@ cudaError_t tb_launch(int dtype, const TbArgs &a, const TbLaunch &L, cudaStream_
 {
     const void *fn = tb_kernel(dtype, L.nc, L.maxc);
     if (!fn) return cudaErrorInvalidConfiguration;
-    static bool prepared[2][6] = {};
+    static bool prepared[2][kNumVariants] = {};
     int vi = 0;
     while (kVariants[vi].nc != L.nc || kVariants[vi].maxc != L.maxc) ++vi;
     if (!prepared[dtype][vi]) {
@@ -383,7 +528,7 @@ cudaError_t tb_launch(int dtype, const TbArgs &a, const TbLaunch &L, cudaStream_
     const int ntz = (a.nz + a.bz - 1) / a.bz;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(a.depth * a.ntx), (unsigned)nty, (unsigned)ntz);
-    cfg.blockDim = dim3((unsigned)(L.nc + kTbThreadsLoader), 1, 1);
+    cfg.blockDim = dim3((unsigned)L.nc, 1, 1);
     cfg.dynamicSmemBytes = L.smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -405,7 +550,7 @@ cudaError_t tb_max_clusters(int dtype, const TbLaunch &L, int depth, int *cluste
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)depth, 1, 1);
-    cfg.blockDim = dim3((unsigned)(L.nc + kTbThreadsLoader), 1, 1);
+    cfg.blockDim = dim3((unsigned)L.nc, 1, 1);
     cfg.dynamicSmemBytes = L.smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;

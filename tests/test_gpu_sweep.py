@@ -56,11 +56,14 @@ PLANS = [
     (J.KERNEL_TB, 5, 5, 7, 9),
     (J.KERNEL_TB, 8, 32, 16, 16),
     (J.KERNEL_TB, 8, 3, 3, 2),
+    (J.KERNEL_TB, 2, 8, 8, 8, 16),
+    (J.KERNEL_TB, 4, 16, 8, 20, 4),
+    (J.KERNEL_TB, 1, 32, 8, 16, 8),
 ]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("plan", PLANS, ids=lambda p: "k%d_d%d_%dx%dx%d" % p)
+@pytest.mark.parametrize("plan", PLANS, ids=lambda p: "k%d_d%d_%dx%dx%d" % p[:5] + ("_r%d" % p[5] if len(p) > 5 else ""))
 def test_fp64_bit_exact_small(shape, plan):
     for T in (1, 2, 3, 7, 12):
         got = _gpu(shape, 11, torch.float64, T, plan)
@@ -116,9 +119,10 @@ def test_argument_errors():
     assert L.jacobi_sweep(h.ptr, pa, pa, 1, s) == -1
     assert L.jacobi_sweep(h.ptr, ctypes.c_void_p(A.data_ptr() + 8), pb, 1, s) == -8
     assert L.jacobi_sweep(h.ptr, pa, ctypes.c_void_p(A.data_ptr() + 16), 1, s) == -1
-    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 0, 8, 8, 8) == -1
-    assert L.jacobi_set_plan(h.ptr, 9, 1, 8, 8, 8) == -1
-    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 8, 512, 512, 8) == -9
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 0, 8, 8, 8, 0) == -1
+    assert L.jacobi_set_plan(h.ptr, 9, 1, 8, 8, 8, 0) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 1, 8, 8, 8, 5) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 8, 512, 512, 8, 0) == -9
 
 
 def test_bounded_wait_timeout_reports_status_and_context_survives():

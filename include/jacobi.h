@@ -119,10 +119,12 @@ int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, i
 /* Reads back the plan jacobi_sweep will use (ring 0 = automatic). */
 int jacobi_get_plan(jacobi_h h, int *kernel, int *depth, int *bx, int *by, int *bz, int *ring);
 
-/* Autotuner (experiment-driven parameter choice, Sect. 2.4): times candidate
- * plans (depth 1..8, tile shapes, z chunks) on the caller's scratch grids
- * (same size as the handle's grids; contents overwritten, never the user's
- * data) and keeps the fastest as the handle's AUTO plan.  Results are
+/* Autotuner (experiment-driven parameter choice, Sect. 2.4): fills the
+ * caller's scratch grids (same size as the handle's grids; contents
+ * overwritten, never the user's data) with a constant and times candidate
+ * plans on them -- the single-pass kernel, and pass kernels of depth 1..8
+ * over tile shapes, then z chunks and ring depths around the best -- and
+ * keeps the fastest as the handle's AUTO plan.  Results are
  * cached per process by (dtype, nx, ny, nz, SM count).  Synchronises
  * stream.  *glups (may be NULL) receives the best measured GLUP/s. */
 int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stream,
@@ -134,6 +136,15 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
  * applies d).  Writes the depths to depths[0..n-1] and returns n, or -1 if
  * more than max_passes passes would be needed or an argument is bad. */
 int jacobi_plan_passes(int T, int depth, int *depths, int max_passes);
+
+/* Self-test of the exact FP64 division used by the FP64 kernels (the sum of
+ * Eq. 1 divided by 6 is computed on the integer pipe): compares it bit for bit with the device's IEEE division for
+ * `count` pseudo-random bit patterns (SplitMix64 stream `seed`, NaNs
+ * skipped) and for mantissas near 2^52, 3*2^51 and 2^53-1 at every exponent
+ * and sign.  Synchronises the device.  *mismatches = number of differing
+ * results; *first_bad (may be NULL) = one failing input's bits. */
+int jacobi_check_division(unsigned long long count, unsigned long long seed,
+                          unsigned long long *mismatches, unsigned long long *first_bad);
 
 /* Reads and clears the handle's device status word (synchronises the
  * device).  *device_status: 0 = fine, else the first JACOBI_ERR_* code a

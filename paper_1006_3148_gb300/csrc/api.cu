@@ -383,11 +383,12 @@ int jacobi_profile_read(jacobi_h h, double *pass_ms, int *pass_launches, int *ot
 
 namespace {
 
-// Times plan p (T = 4*depth sweeps, best of two after a warm-up) in GLUP/s.
+// Times plan p (T = max(8, 4*depth) sweeps, best of two after a warm-up) in
+// GLUP/s.
 int time_plan(jacobi_plan_s *h, const Plan &p, void *A, void *B, cudaStream_t s, cudaEvent_t e0,
               cudaEvent_t e1, double *glups)
 {
-    const int T = 4 * p.depth;
+    const int T = (4 * p.depth > 8) ? 4 * p.depth : 8;
     int st = run_sweeps(h, p, A, B, T, s);
     if (st != JACOBI_OK) return st;
     float best = 1e30f;
@@ -437,6 +438,15 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
         cudaEventDestroy(e0);
         return cuda_fail(e);
     }
+    // Benign, finite, normal values (uninitialised scratch could hold NaNs
+    // or subnormals, which take slower arithmetic paths).
+    e = fill_launch(h->dtype, scratchA, (long long)grid_elems(h), 0.5, s);
+    if (e == cudaSuccess) e = fill_launch(h->dtype, scratchB, (long long)grid_elems(h), 0.5, s);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(e);
+    }
     double best = -1.0;
     Plan bestp;
     int st = JACOBI_OK;
@@ -451,6 +461,13 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
     };
     const int *dl = f64 ? depths64 : depths32;
     const int nd = f64 ? 3 : 5;
+    {
+        Plan p;  // the single-pass kernel competes too
+        p.kernel = JACOBI_KERNEL_PLAIN;
+        p.depth = 1;
+        p.bx = p.by = p.bz = 1;
+        consider(p);
+    }
     for (int di = 0; di < nd; ++di)
         for (const auto &t : tiles) {
             Plan p;
@@ -461,7 +478,7 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
             p.ring = 0;
             consider(clampp(p));
         }
-    if (st == JACOBI_OK && best > 0) {
+    if (st == JACOBI_OK && best > 0 && bestp.kernel == JACOBI_KERNEL_TB) {
         const Plan base = bestp;
         for (int bz : bzs)
             for (int rg : rings) {

@@ -2,13 +2,41 @@
 // intrinsics keep the compiler from contracting or reassociating: the six
 // neighbours are added left to right in the printed order (i-1, i+1, j-1,
 // j+1, k-1, k+1).
-//   FP64: the sum is divided by 6.0 (IEEE quotient, round to nearest), so
-//         results are bit-identical to a plain CPU loop.
+//   FP64: the sum is divided by 6.0 (IEEE quotient, round to nearest, via
+//         div6_rn), so results are bit-identical to a plain CPU loop.
 //   FP32: the sum is multiplied by RN_f32(1/6) (one multiplication and five
 //         additions, the count of Sect. 2.3).
 #pragma once
 
 namespace jac {
+
+// Correctly rounded s / 6 in binary64 (round to nearest even), computed on
+// the integer pipe.  For a finite normal s = +-M * 2^(E-1075), M = 2^52 +
+// mantissa, the quotient is (M/3) * 2^(E-1076).  Its 53-bit significand is
+// N = RN(K*M/3) with K = 2 when M >= 3*2^51 (then K*M/3 lies in
+// [2^52, 2^52.42)) and K = 4 otherwise (K*M/3 in [2^52.42, 2^53 - 4/3]);
+// the result is N * 2^(E-1077) or N * 2^(E-1078), i.e. biased exponent
+// E-2 or E-3.  X/3 for an integer X has remainder 0, 1 or 2, so it is never
+// halfway between integers and RN(X/3) = floor((X + 1)/3): no tie rule is
+// needed.  floor(Y/3) for 64-bit Y is the high half of Y * 0xAAAA...AAB
+// shifted right by one (division by an invariant integer through a
+// multiplication, Granlund and Montgomery, PLDI 1994).  Zero returns
+// itself; subnormal and tiny sums (E < 4, whose quotient may be subnormal),
+// infinities and NaNs take the IEEE division instead.  Exhaustively structured tests compare
+// this with __ddiv_rn (jacobi_check_division).
+__device__ __forceinline__ double div6_rn(double s)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+    const unsigned E = (unsigned)(b >> 52) & 0x7FFu;
+    if (E - 4u > 2042u) return ((b << 1) == 0ull) ? s : __ddiv_rn(s, 6.0);  // +-0 / 6 = +-0
+    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const unsigned small = (M < 0x18000000000000ull) ? 1u : 0u;  // M < 3 * 2^51
+    const unsigned long long X = (M << (1u + small)) + 1ull;
+    const unsigned long long N = __umul64hi(X, 0xAAAAAAAAAAAAAAABull) >> 1;
+    const unsigned long long r =
+        (b & 0x8000000000000000ull) | ((((unsigned long long)(E - 3u - small)) << 52) + N);
+    return __longlong_as_double((long long)r);
+}
 
 template <typename T>
 struct Arith;
@@ -23,7 +51,7 @@ struct Arith<double> {
         a = __dadd_rn(a, n);
         a = __dadd_rn(a, b);
         a = __dadd_rn(a, t);
-        return __ddiv_rn(a, 6.0);
+        return div6_rn(a);
     }
 };
 

@@ -71,6 +71,14 @@ __global__ void halo_copy_kernel(const T *__restrict__ A, T *__restrict__ B, int
     }
 }
 
+// ------------------------------------------------------------------ fill
+template <typename T>
+__global__ void fill_kernel(T *p, long long n, T v)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
 // ----------------------------------------------------------------- plain
 template <typename T>
 __global__ void __launch_bounds__(256) plain_pass_kernel(const PlainArgs a)
@@ -584,6 +592,14 @@ cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, 
     else
         halo_copy_kernel<float><<<grid, block, 0, s>>>(static_cast<const float *>(A), static_cast<float *>(B), nx, ny,
                                                         nz);
+    return cudaGetLastError();
+}
+
+cudaError_t fill_launch(int dtype, void *p, long long n, double v, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, 152 * 16);
+    if (dtype == JACOBI_F64) fill_kernel<double><<<grid, 256, 0, s>>>(static_cast<double *>(p), n, v);
+    else fill_kernel<float><<<grid, 256, 0, s>>>(static_cast<float *>(p), n, (float)v);
     return cudaGetLastError();
 }
 

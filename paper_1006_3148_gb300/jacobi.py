@@ -70,6 +70,8 @@ def load(build_if_missing: bool = True):
             "jacobi_debug_set_fault": ([P, i, i], i),
             "jacobi_plan_passes": ([i, i, pi, i], i),
             "jacobi_profile_enable": ([P, i], i),
+            "jacobi_check_division": ([ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong),
+                                       ctypes.POINTER(ctypes.c_ulonglong)], i),
             "jacobi_profile_read": ([P, ctypes.POINTER(d), pi, pi], i),
         }
         for name, (args, res) in sig.items():
@@ -216,3 +218,11 @@ def jacobi_profile_read(h: Handle) -> dict:
     _check(load().jacobi_profile_read(h.ptr, ctypes.byref(ms), ctypes.byref(npass), ctypes.byref(nother)),
            "jacobi_profile_read")
     return {"pass_ms": ms.value, "pass_launches": npass.value, "other_launches": nother.value}
+
+
+def jacobi_check_division(count: int, seed: int = 1) -> tuple:
+    """(mismatches, first failing input bits) of the exact FP64 division."""
+    m, f = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+    _check(load().jacobi_check_division(int(count), int(seed), ctypes.byref(m), ctypes.byref(f)),
+           "jacobi_check_division")
+    return m.value, f.value

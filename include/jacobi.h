@@ -170,6 +170,53 @@ int jacobi_profile_read(jacobi_h h, double *pass_ms, int *pass_launches, int *ot
  * of later launches (default 2000). */
 int jacobi_debug_set_fault(jacobi_h h, int mode, int limit_ms);
 
+/* ---------------------------------------------------------------- batch
+ * Many independent grids (each its own size, element type and sweep count
+ * T_g) swept in ONE persistent kernel launch that a CUDA graph replays.
+ * Work items are (grid, x-y tile column, sweep), taken in pass-major order
+ * from a device-side queue; an item waits (bounded) until its tile and the
+ * four face-neighbour tiles finished the previous sweep -- per-tile
+ * progress counters, the counters c_i of the relaxed synchronisation of
+ * Sect. 2.2.  Each grid ends exactly as after jacobi_sweep with T_g sweeps:
+ * result in B_g if T_g is odd, else in A_g. */
+
+/* Creates a batch of n (1..65535) grids; nx/ny/nz/dtype/T are host arrays
+ * of n entries (sizes >= 1, dtype JACOBI_F64/F32, T >= 0, each grid below
+ * 2^31 elements).  Allocates the device descriptor table and counters and
+ * captures the graph (item-counter reset, halo copy of every grid,
+ * persistent launch).  Synchronous. */
+int jacobi_batch_create(jacobi_batch_h *out, int n, const int *nx, const int *ny, const int *nz,
+                        const int *dtype, const int *T);
+
+/* Binds the grids and launches the graph on stream.  A, B: host arrays of
+ * n device pointers (grid g: (nx+2)(ny+2)(nz+2) elements of its dtype,
+ * A[g] != B[g]); the pointer table is copied to the device on stream before
+ * the graph launch.  Asynchronous.  Runs of one batch must not overlap. */
+int jacobi_batch_run(jacobi_batch_h b, void *const *A, void *const *B, jacobi_stream_t stream);
+
+/* Frees the batch (after the caller synchronised its streams). */
+int jacobi_batch_destroy(jacobi_batch_h b);
+
+/* Tile of a work item (bx*by cells, bx*by <= 4096); re-captures the graph. */
+int jacobi_batch_set_tile(jacobi_batch_h b, int bx, int by);
+
+/* Autotuner for the batch: fills the caller's scratch grids (arrays of n
+ * device pointers, same shapes as the batch) with a constant, times the
+ * candidate tiles and keeps the fastest.  Synchronises stream. */
+int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scratchB,
+                      jacobi_stream_t stream, double *glups);
+
+/* Current tile, number of work items and persistent CTAs (any may be NULL). */
+int jacobi_batch_get_info(jacobi_batch_h b, int *bx, int *by, long long *items, int *blocks);
+
+/* Reads and clears the batch's device status word (synchronises). */
+int jacobi_batch_get_status(jacobi_batch_h b, int *device_status);
+
+/* Test hook: mode 1 makes the persistent kernel never publish sweep 2 of
+ * the first tile, so that dependent waits run out after limit_ms and the
+ * kernel records JACOBI_ERR_TIMEOUT (no fault); re-captures the graph. */
+int jacobi_batch_debug_set_fault(jacobi_batch_h b, int mode, int limit_ms);
+
 #ifdef __cplusplus
 }
 #endif

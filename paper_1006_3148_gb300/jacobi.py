@@ -70,6 +70,14 @@ def load(build_if_missing: bool = True):
             "jacobi_debug_set_fault": ([P, i, i], i),
             "jacobi_plan_passes": ([i, i, pi, i], i),
             "jacobi_profile_enable": ([P, i], i),
+            "jacobi_batch_create": ([ctypes.POINTER(P), i, pi, pi, pi, pi, pi], i),
+            "jacobi_batch_run": ([P, ctypes.POINTER(P), ctypes.POINTER(P), P], i),
+            "jacobi_batch_destroy": ([P], i),
+            "jacobi_batch_set_tile": ([P, i, i], i),
+            "jacobi_batch_tune": ([P, ctypes.POINTER(P), ctypes.POINTER(P), P, ctypes.POINTER(d)], i),
+            "jacobi_batch_get_info": ([P, pi, pi, ctypes.POINTER(ctypes.c_longlong), pi], i),
+            "jacobi_batch_get_status": ([P, pi], i),
+            "jacobi_batch_debug_set_fault": ([P, i, i], i),
             "jacobi_check_division": ([ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong),
                                        ctypes.POINTER(ctypes.c_ulonglong)], i),
             "jacobi_profile_read": ([P, ctypes.POINTER(d), pi, pi], i),
@@ -226,3 +234,90 @@ def jacobi_check_division(count: int, seed: int = 1) -> tuple:
     _check(load().jacobi_check_division(int(count), int(seed), ctypes.byref(m), ctypes.byref(f)),
            "jacobi_check_division")
     return m.value, f.value
+
+
+class Batch:
+    """Owns a jacobi_batch_h for grids of the given sizes, dtypes and sweeps."""
+
+    def __init__(self, dims, dtypes, Ts):
+        L = load()
+        n = len(dims)
+        arr = lambda xs: (ctypes.c_int * n)(*xs)
+        self.n = n
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        self.dtypes = [torch.float64 if _dtype_code(t) == F64 else torch.float32 for t in dtypes]
+        self.Ts = [int(t) for t in Ts]
+        h = ctypes.c_void_p()
+        _check(L.jacobi_batch_create(ctypes.byref(h), n, arr([d[0] for d in self.dims]),
+                                     arr([d[1] for d in self.dims]), arr([d[2] for d in self.dims]),
+                                     arr([_dtype_code(t) for t in self.dtypes]), arr(self.Ts)),
+               "jacobi_batch_create")
+        self._h = h
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def shape(self, g):
+        nx, ny, nz = self.dims[g]
+        return (nz + 2, ny + 2, nx + 2)
+
+    def _ptrs(self, grids):
+        if len(grids) != self.n:
+            raise ValueError("need %d grids" % self.n)
+        return (ctypes.c_void_p * self.n)(*[_grid_ptr(t, self.shape(g), self.dtypes[g]).value
+                                            for g, t in enumerate(grids)])
+
+    def close(self):
+        if self._h:
+            load().jacobi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def jacobi_batch_create(dims, dtypes, Ts) -> Batch:
+    return Batch(dims, dtypes, Ts)
+
+
+def jacobi_batch_run(b: Batch, A, B, stream=None):
+    """Runs all sweeps; returns the list of result grids (B_g if T_g odd)."""
+    pa, pb = b._ptrs(A), b._ptrs(B)
+    _check(load().jacobi_batch_run(b.ptr, pa, pb, _stream(stream)), "jacobi_batch_run")
+    return [B[g] if b.Ts[g] % 2 == 1 else A[g] for g in range(b.n)]
+
+
+def jacobi_batch_destroy(b: Batch):
+    b.close()
+
+
+def jacobi_batch_set_tile(b: Batch, bx: int, by: int):
+    _check(load().jacobi_batch_set_tile(b.ptr, int(bx), int(by)), "jacobi_batch_set_tile")
+
+
+def jacobi_batch_tune(b: Batch, scratchA, scratchB, stream=None) -> float:
+    g = ctypes.c_double()
+    _check(load().jacobi_batch_tune(b.ptr, b._ptrs(scratchA), b._ptrs(scratchB), _stream(stream),
+                                    ctypes.byref(g)), "jacobi_batch_tune")
+    return g.value
+
+
+def jacobi_batch_get_info(b: Batch) -> dict:
+    bx, by, blocks, items = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _check(load().jacobi_batch_get_info(b.ptr, ctypes.byref(bx), ctypes.byref(by), ctypes.byref(items),
+                                        ctypes.byref(blocks)), "jacobi_batch_get_info")
+    return {"bx": bx.value, "by": by.value, "items": items.value, "blocks": blocks.value}
+
+
+def jacobi_batch_get_status(b: Batch) -> int:
+    v = ctypes.c_int()
+    _check(load().jacobi_batch_get_status(b.ptr, ctypes.byref(v)), "jacobi_batch_get_status")
+    return v.value
+
+
+def jacobi_batch_debug_set_fault(b: Batch, mode: int, limit_ms: int = 2000):
+    _check(load().jacobi_batch_debug_set_fault(b.ptr, int(mode), int(limit_ms)), "jacobi_batch_debug_set_fault")

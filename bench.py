@@ -46,6 +46,8 @@ WORKLOADS = {
                     name="jacobi3d_fp64_64cubed_T10"),
     "fp32_1024": dict(n=(1024, 1024, 1024), dtype="f32", T=200, gen="mode", seed=3,
                       name="jacobi3d_fp32_1024cubed_T200_mode16"),
+    "batch256": dict(n=None, dtype="mixed", T=50, gen="batch", seed=4,
+                     name="jacobi3d_batch_256grids_32to192_half_fp64_T50"),
 }
 
 
@@ -352,6 +354,138 @@ def run_ours(args, w):
     return 0
 
 
+def run_batch(args, w):
+    """256 independent grids (sizes U{32..192} per axis, half FP64 / half
+    FP32, interior and halo U[0,1), T = 50 each): one step = one
+    jacobi_batch_run (one persistent launch replayed from a CUDA graph)."""
+    import torch
+    import numpy as np
+    from paper_1006_3148_gb300 import inputs
+    from paper_1006_3148_gb300 import jacobi as J
+
+    dist, rank, ws, local = _dist()
+    if dist is not None:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dims, f32 = inputs.batch_dims(256, seed=w["seed"])
+    T = w["T"]
+    dts = [torch.float32 if f else torch.float64 for f in f32]
+    b = J.Batch(dims, dts, [T] * len(dims))
+    A = [inputs.uniform_grid(*d, seed=1000 + g, dtype=torch.float64, device=dev).to(dts[g])
+         for g, d in enumerate(dims)]
+    B = [torch.empty_like(x) for x in A]
+    tune = None
+    if not args.no_tune:
+        sa = [torch.empty_like(x) for x in A]
+        sb = [torch.empty_like(x) for x in A]
+        tune = J.jacobi_batch_tune(b, sa, sb)
+        del sa, sb
+        torch.cuda.empty_cache()
+    info = J.jacobi_batch_get_info(b)
+    lups = float(sum(nx * ny * nz for nx, ny, nz in dims)) * T
+    lups64 = float(sum(nx * ny * nz for (nx, ny, nz), f in zip(dims, f32) if not f)) * T
+    bytes_alg = float(sum(2 * (4 if f else 8) * nx * ny * nz for (nx, ny, nz), f in zip(dims, f32))) * T
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        J.jacobi_batch_run(b, A, B, stream)
+    barrier()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        J.jacobi_batch_run(b, A, B, stream)
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    assert J.jacobi_batch_get_status(b) == 0
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    step_s = ms * 1e-3 / args.steps
+    value = ws * lups / step_s / 1e9
+    peaks, peak_src = _peaks()
+    m_s = float(peaks.get("hbm_gbs", M_S_FALLBACK))
+    hbm_ach = bytes_alg / step_s / 1e9
+    alu_peak = FP64_LANES_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 1e12
+    alu_ach = 5.0 * lups64 / step_s / 1e12
+    if alu_ach / alu_peak > hbm_ach / m_s:
+        roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
+                "traffic": None, "note": "FP64 pipe, 5 FP64 additions per FP64 LUP (the division runs on the "
+                "integer pipe); the launch also sweeps the FP32 grids",
+                "hbm": {"achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s}}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
+                "traffic": None, "peak_source": peak_src}
+    roof["kernel"] = "batch_kernel"
+    roof["avg_launch_ms"] = step_s * 1e3
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": w["name"], "grids": len(dims), "T": T, "fp32_grids": int(sum(f32)),
+                   "cells": int(sum(nx * ny * nz for nx, ny, nz in dims)), "tile": [info["bx"], info["by"], info["bz"]],
+                   "items": info["items"], "persistent_ctas": info["blocks"],
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (%.2f GB of grids)" % (2 * sum(x.numel() * x.element_size()
+                                                                            for x in A) / 1e9)},
+        "roofline": roof, "gpu_launches": 2 * args.steps, "clocks": clocks,
+    }
+    if tune is not None:
+        line["tuner_best_glups"] = tune
+    if not args.no_e2e:
+        hosts = [x.cpu().pin_memory() for x in A]
+        outs_h = [torch.empty_like(x).pin_memory() for x in hosts]
+        barrier()
+        ke = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            for g in range(len(A)):
+                A[g].copy_(hosts[g], non_blocking=True)
+            outs = J.jacobi_batch_run(b, A, B, stream)
+            for g in range(len(A)):
+                outs_h[g].copy_(outs[g], non_blocking=True)
+            torch.cuda.synchronize()
+        dt_e = time.perf_counter() - t0
+        nbytes = sum(x.numel() * x.element_size() for x in hosts)
+        line["e2e"] = {"value": ws * lups * ke / dt_e / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": nbytes, "steps": ke}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        done = 0.0
+        ng = 0
+        for g, (nx, ny, nz) in enumerate(dims):
+            a = inputs.uniform_grid(nx, ny, nz, seed=1000 + g).to(dts[g]).numpy()
+            oracle.jacobi(a, np.empty_like(a), T)
+            done += nx * ny * nz * T
+            ng += 1
+            if time.perf_counter() - t0 > args.cpu_budget:
+                break
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / dt / 1e9, "unit": "GLUP/s", "cores": oracle.threads(),
+                                "kind": "oracle", "sample": "first %d of the 256 grids, %d sweeps each" % (ng, T)}
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -378,7 +512,11 @@ def main():
         w["T"] = args.T
         w["name"] += "_T%d" % args.T
     if args.impl == "reference":
+        if w["gen"] == "batch":
+            return run_reference(args, dict(WORKLOADS["fp64_512"]))
         return run_reference(args, w)
+    if w["gen"] == "batch":
+        return run_batch(args, w)
     return run_ours(args, w)
 
 

@@ -170,6 +170,37 @@ int jacobi_profile_read(jacobi_h h, double *pass_ms, int *pass_launches, int *ot
  * of later launches (default 2000). */
 int jacobi_debug_set_fault(jacobi_h h, int mode, int limit_ms);
 
+/* -------------------------------------------------------------- Poisson
+ * -Lap_h u = f with the 7-point Laplacian, (A_h u) = (6u - sum of the six
+ * neighbours)/h^2, on a handle created with JACOBI_F64; the halo of u holds
+ * the Dirichlet values (0 for the homogeneous problem); f's halo is not
+ * read.  Scratch grids are allocated on the handle at first use. */
+
+/* *rel = ||f - A_h u||_2 / ||f||_2 over the interior, FP64, sums of squares
+ * reduced in a fixed order.  Synchronises stream. */
+int jacobi_poisson_residual(jacobi_h h, const void *u, const void *f, double hgrid,
+                            jacobi_stream_t stream, double *rel);
+
+/* Plain FP64 Jacobi for the Poisson problem: `sweeps` sweeps of
+ * u <- (neighbour sum + h^2 f)/6 (order of Eq. 1, h^2 f added last, IEEE
+ * division), u and tmp in turn, all in one persistent launch; result in tmp
+ * if sweeps is odd, else in u (tmp's halo is set from u's).  Asynchronous. */
+int jacobi_poisson_jacobi(jacobi_h h, void *u, void *tmp, const void *f, double hgrid, int sweeps,
+                          jacobi_stream_t stream);
+
+/* Mixed-precision iterative refinement (u updated in place):
+ *   loop: r = f - A_h u in FP64, rel = ||r||/||f||; stop if rel <= rel_tol
+ *         or max_outer corrections were applied; g = RN_f32(h^2 r);
+ *         e = 0 and inner_sweeps FP32 Jacobi sweeps e <- (sum(e) + g)/6 on
+ *         A_h e = r (zero halo, one persistent launch); u += (double)e.
+ * Only the residual and the update run in FP64.  *outer_done = corrections
+ * applied, *final_rel_residual = last rel (both may be NULL).  Returns
+ * JACOBI_ERR_NOT_CONVERGED if rel_tol was not reached.  Synchronises stream
+ * once per outer step (to read the residual norm). */
+int jacobi_refine(jacobi_h h, double *u, const double *f, double hgrid, double rel_tol,
+                  int inner_sweeps, int max_outer, jacobi_stream_t stream, int *outer_done,
+                  double *final_rel_residual);
+
 /* ---------------------------------------------------------------- batch
  * Many independent grids (each its own size, element type and sweep count
  * T_g) swept in ONE persistent kernel launch that a CUDA graph replays.
@@ -194,11 +225,21 @@ int jacobi_batch_create(jacobi_batch_h *out, int n, const int *nx, const int *ny
  * the graph launch.  Asynchronous.  Runs of one batch must not overlap. */
 int jacobi_batch_run(jacobi_batch_h b, void *const *A, void *const *B, jacobi_stream_t stream);
 
+/* Same, for the Poisson problem -Lap_h u = f: grid g is swept with the
+ * source term RHS[g] (device pointer, same shape and dtype, holding
+ * g = h^2 f; halo ignored), i.e. update = (neighbour sum + g)/6 in the
+ * order of Eq. (1) with g added last.  RHS = NULL or RHS[g] = NULL: plain
+ * Jacobi for that grid. */
+int jacobi_batch_run_rhs(jacobi_batch_h b, void *const *A, void *const *B, const void *const *RHS,
+                         jacobi_stream_t stream);
+
 /* Frees the batch (after the caller synchronised its streams). */
 int jacobi_batch_destroy(jacobi_batch_h b);
 
-/* Tile of a work item (bx*by cells, bx*by <= 4096); re-captures the graph. */
-int jacobi_batch_set_tile(jacobi_batch_h b, int bx, int by);
+/* Tile of a work item: bx*by cells (bx*by <= 4096) of bz planes (bz = 0:
+ * the whole z column; bz > 0 also splits z, and an item then also waits on
+ * the tiles above and below).  Re-captures the graph. */
+int jacobi_batch_set_tile(jacobi_batch_h b, int bx, int by, int bz);
 
 /* Autotuner for the batch: fills the caller's scratch grids (arrays of n
  * device pointers, same shapes as the batch) with a constant, times the
@@ -207,7 +248,7 @@ int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scra
                       jacobi_stream_t stream, double *glups);
 
 /* Current tile, number of work items and persistent CTAs (any may be NULL). */
-int jacobi_batch_get_info(jacobi_batch_h b, int *bx, int *by, long long *items, int *blocks);
+int jacobi_batch_get_info(jacobi_batch_h b, int *bx, int *by, int *bz, long long *items, int *blocks);
 
 /* Reads and clears the batch's device status word (synchronises). */
 int jacobi_batch_get_status(jacobi_batch_h b, int *device_status);

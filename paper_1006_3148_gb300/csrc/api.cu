@@ -16,20 +16,6 @@
 
 using namespace jac;
 
-struct jacobi_plan_s {
-    int nx = 0, ny = 0, nz = 0, dtype = 0, device = 0, sms = 0;
-    Plan plan;
-    bool forced = false;
-    int *d_status = nullptr;
-    int fault_mode = 0;
-    unsigned long long limit_ns = 2000000000ull;
-    void *hostA = nullptr, *hostB = nullptr;  // device grids of jacobi_sweep_host
-    bool prof = false;                          // profiling of pass launches
-    std::vector<cudaEvent_t> ev_pool;           // events, reused after a read
-    size_t ev_used = 0;
-    int prof_pass = 0, prof_other = 0;
-};
-
 namespace {
 
 thread_local std::string g_last_cuda;
@@ -247,6 +233,7 @@ int jacobi_destroy(jacobi_h h)
     if (h->hostA) cudaFree(h->hostA);
     if (h->hostB) cudaFree(h->hostB);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    free_poisson_scratch(h);
     delete h;
     return JACOBI_OK;
 }

@@ -53,6 +53,18 @@ struct Arith<double> {
         a = __dadd_rn(a, t);
         return div6_rn(a);
     }
+    // Jacobi for the Poisson problem: (neighbour sum + g) / 6, g = h^2 f.
+    static __device__ __forceinline__ double update_rhs(double w, double e, double s, double n, double b,
+                                                        double t, double g)
+    {
+        double a = __dadd_rn(w, e);
+        a = __dadd_rn(a, s);
+        a = __dadd_rn(a, n);
+        a = __dadd_rn(a, b);
+        a = __dadd_rn(a, t);
+        a = __dadd_rn(a, g);
+        return div6_rn(a);
+    }
 };
 
 template <>
@@ -64,6 +76,17 @@ struct Arith<float> {
         a = __fadd_rn(a, n);
         a = __fadd_rn(a, b);
         a = __fadd_rn(a, t);
+        return __fmul_rn(a, 1.0f / 6.0f);
+    }
+    static __device__ __forceinline__ float update_rhs(float w, float e, float s, float n, float b, float t,
+                                                       float g)
+    {
+        float a = __fadd_rn(w, e);
+        a = __fadd_rn(a, s);
+        a = __fadd_rn(a, n);
+        a = __fadd_rn(a, b);
+        a = __fadd_rn(a, t);
+        a = __fadd_rn(a, g);
         return __fmul_rn(a, 1.0f / 6.0f);
     }
 };

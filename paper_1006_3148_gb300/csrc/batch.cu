@@ -2,11 +2,12 @@
 // types, all T_g sweeps of all grids in ONE persistent launch, replayed from
 // a CUDA graph.
 //
-// Work items are (grid g, x-y tile t of g, sweep p), numbered pass-major:
+// Work items are (grid g, tile t of g, sweep p), numbered pass-major:
 // item = p * total_tiles + (tile_base[g] + t).  Resident CTAs take items
 // from a global atomic counter, so items are started in that order.  Item
 // (g, t, p) reads grid buffer p%2 and writes buffer (p+1)%2 on the tile's
-// cells for all z; it may start once tile t and its four face neighbours
+// cells (bx*by*bz; bz = nz unless z is split); it may start once tile t and
+// its face neighbours
 // (the only tiles whose cells the 7-point stencil reads) have finished
 // sweep p-1: that covers the cells it reads (read after write) and the cells
 // the neighbours' sweep p-1 still reads in the buffer it overwrites (write
@@ -30,8 +31,9 @@ namespace jac {
 struct BatchGrid {
     void *A;
     void *B;
+    const void *rhs;  // optional source term g (same dtype): update (sum + g)/6
     int nx, ny, nz, dtype, T;
-    int ntx, nty;
+    int ntx, nty, ntz;
     int tile_base;  // global index of this grid's tile 0
 };
 
@@ -40,7 +42,7 @@ struct BatchArgs {
     int ngrids;
     int total_tiles;
     long long total_items;
-    int bx, by;  // tile interior size
+    int bx, by, bz;  // tile interior size
     int *head;   // next item
     int *progress;
     int *status;
@@ -78,27 +80,33 @@ __device__ bool wait_progress(const int *progress, int i, int want, unsigned lon
     }
 }
 
-// One sweep of one tile column: thread (lx, ly) walks z with the values at
-// k-1, k, k+1 of its column in registers; in-plane neighbours are read
-// through L2 (.cg: other CTAs rewrote this buffer two sweeps ago).
+// One sweep of one tile: thread (lx, ly) walks z over the tile's planes with
+// the values at k-1, k, k+1 of its column in registers; in-plane neighbours
+// are read through L2 (.cg: other CTAs rewrote this buffer two sweeps ago).
 template <typename T>
-__device__ void sweep_tile(const BatchGrid &G, int tx, int ty, int p, int bx, int by)
+__device__ void sweep_tile(const BatchGrid &G, int tx, int ty, int tz, int p, int bx, int by, int bz)
 {
     const T *src = static_cast<const T *>((p % 2 == 0) ? G.A : G.B);
     T *dst = static_cast<T *>((p % 2 == 0) ? G.B : G.A);
+    const T *rhs = static_cast<const T *>(G.rhs);
     const long long NXP = G.nx + 2, plane = NXP * (G.ny + 2);
     const int nthreads = blockDim.x;
-    const int x0 = 1 + tx * bx, y0 = 1 + ty * by;
-    const int w = min(bx, G.nx + 1 - x0), hgt = min(by, G.ny + 1 - y0);
+    const int x0 = 1 + tx * bx, y0 = 1 + ty * by, z0 = 1 + tz * bz;
+    const int w = min(bx, G.nx + 1 - x0), hgt = min(by, G.ny + 1 - y0), z1 = min(z0 + bz, G.nz + 1);
     for (int c = threadIdx.x; c < w * hgt; c += nthreads) {
         const int x = x0 + c % w, y = y0 + c / w;
         const T *col = src + (long long)y * NXP + x;
         T *ocol = dst + (long long)y * NXP + x;
-        T a = __ldcg(col), b = __ldcg(col + plane);
-        for (int k = 1; k <= G.nz; ++k) {
+        T a = __ldcg(col + (long long)(z0 - 1) * plane), b = __ldcg(col + (long long)z0 * plane);
+        for (int k = z0; k < z1; ++k) {
             const T *cp = col + k * plane;
             const T cnext = __ldcg(cp + plane);
-            const T v = Arith<T>::update(__ldcg(cp - 1), __ldcg(cp + 1), __ldcg(cp - NXP), __ldcg(cp + NXP), a, cnext);
+            T v;
+            if (rhs)
+                v = Arith<T>::update_rhs(__ldcg(cp - 1), __ldcg(cp + 1), __ldcg(cp - NXP), __ldcg(cp + NXP), a, cnext,
+                                         __ldg(rhs + (cp - src)));
+            else
+                v = Arith<T>::update(__ldcg(cp - 1), __ldcg(cp + 1), __ldcg(cp - NXP), __ldcg(cp + NXP), a, cnext);
             ocol[k * plane] = v;
             a = b;
             b = cnext;
@@ -127,7 +135,8 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs a)
             else hi = mid - 1;
         }
         const BatchGrid G = a.grids[lo];
-        const int t = tg - G.tile_base, tx = t % G.ntx, ty = t / G.ntx;
+        const int t = tg - G.tile_base, txy = G.ntx * G.nty;
+        const int tx = t % G.ntx, ty = (t / G.ntx) % G.nty, tz = t / txy;
         if (p >= G.T) continue;  // this grid is done; nothing waits on it
         if (threadIdx.x == 0) {
             bool ok = true;
@@ -138,14 +147,16 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs a)
                 if (tx + 1 < G.ntx) ok = ok && wait_progress(a.progress, tg + 1, want, a.limit_ns, vstatus);
                 if (ty > 0) ok = ok && wait_progress(a.progress, tg - G.ntx, want, a.limit_ns, vstatus);
                 if (ty + 1 < G.nty) ok = ok && wait_progress(a.progress, tg + G.ntx, want, a.limit_ns, vstatus);
+                if (tz > 0) ok = ok && wait_progress(a.progress, tg - txy, want, a.limit_ns, vstatus);
+                if (tz + 1 < G.ntz) ok = ok && wait_progress(a.progress, tg + txy, want, a.limit_ns, vstatus);
             }
             if (!ok) atomicCAS(a.status, 0, JACOBI_ERR_TIMEOUT);
             s_ok = ok;
         }
         __syncthreads();
         if (s_ok) {
-            if (G.dtype == JACOBI_F64) sweep_tile<double>(G, tx, ty, p, a.bx, a.by);
-            else sweep_tile<float>(G, tx, ty, p, a.bx, a.by);
+            if (G.dtype == JACOBI_F64) sweep_tile<double>(G, tx, ty, tz, p, a.bx, a.by, a.bz);
+            else sweep_tile<float>(G, tx, ty, tz, p, a.bx, a.by, a.bz);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -181,7 +192,7 @@ using namespace jac;
 struct jacobi_batch_s {
     int n = 0;
     std::vector<BatchGrid> grids;  // host copy (pointers bound by jacobi_batch_run)
-    int bx = 32, by = 8;
+    int bx = 32, by = 8, bz = 0;  // bz 0: whole z column per item
     int total_tiles = 0, max_T = 0;
     long long total_items = 0;
     BatchGrid *d_grids = nullptr;
@@ -205,8 +216,9 @@ void layout(jacobi_batch_s *b)
     for (BatchGrid &G : b->grids) {
         G.ntx = (G.nx + b->bx - 1) / b->bx;
         G.nty = (G.ny + b->by - 1) / b->by;
+        G.ntz = (b->bz > 0) ? (G.nz + b->bz - 1) / b->bz : 1;
         G.tile_base = base;
-        base += G.ntx * G.nty;
+        base += G.ntx * G.nty * G.ntz;
         b->max_T = std::max(b->max_T, G.T);
     }
     b->total_tiles = base;
@@ -247,6 +259,7 @@ int build_graph(jacobi_batch_s *b)
     a.total_items = b->total_items;
     a.bx = b->bx;
     a.by = b->by;
+    a.bz = (b->bz > 0) ? b->bz : (1 << 30);
     a.head = b->d_ctl;
     a.status = b->d_ctl + 1;
     a.progress = b->d_ctl + 2;
@@ -296,6 +309,7 @@ int jacobi_batch_create(jacobi_batch_h *out, int n, const int *nx, const int *ny
     for (int g = 0; g < n; ++g) {
         BatchGrid &G = b->grids[(size_t)g];
         G.A = G.B = nullptr;
+        G.rhs = nullptr;
         G.nx = nx[g];
         G.ny = ny[g];
         G.nz = nz[g];
@@ -329,13 +343,15 @@ int jacobi_batch_destroy(jacobi_batch_h b)
     return JACOBI_OK;
 }
 
-int jacobi_batch_run(jacobi_batch_h b, void *const *A, void *const *B, jacobi_stream_t stream)
+int jacobi_batch_run_rhs(jacobi_batch_h b, void *const *A, void *const *B, const void *const *RHS,
+                         jacobi_stream_t stream)
 {
     if (!b || !A || !B) return JACOBI_ERR_ARG;
     for (int g = 0; g < b->n; ++g) {
         if (!A[g] || !B[g] || A[g] == B[g]) return JACOBI_ERR_ARG;
         b->grids[(size_t)g].A = A[g];
         b->grids[(size_t)g].B = B[g];
+        b->grids[(size_t)g].rhs = RHS ? RHS[g] : nullptr;
     }
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(b->d_grids, b->grids.data(), sizeof(BatchGrid) * (size_t)b->n,
@@ -348,20 +364,27 @@ int jacobi_batch_run(jacobi_batch_h b, void *const *A, void *const *B, jacobi_st
     return JACOBI_OK;
 }
 
-int jacobi_batch_set_tile(jacobi_batch_h b, int bx, int by)
+int jacobi_batch_run(jacobi_batch_h b, void *const *A, void *const *B, jacobi_stream_t stream)
 {
-    if (!b || bx < 1 || by < 1 || bx * by > 4096) return JACOBI_ERR_ARG;
+    return jacobi_batch_run_rhs(b, A, B, nullptr, stream);
+}
+
+int jacobi_batch_set_tile(jacobi_batch_h b, int bx, int by, int bz)
+{
+    if (!b || bx < 1 || by < 1 || bz < 0 || bx * by > 4096) return JACOBI_ERR_ARG;
     b->bx = bx;
     b->by = by;
+    b->bz = bz;
     layout(b);
     return build_graph(b);
 }
 
-int jacobi_batch_get_info(jacobi_batch_h b, int *bx, int *by, long long *items, int *blocks)
+int jacobi_batch_get_info(jacobi_batch_h b, int *bx, int *by, int *bz, long long *items, int *blocks)
 {
     if (!b) return JACOBI_ERR_ARG;
     if (bx) *bx = b->bx;
     if (by) *by = b->by;
+    if (bz) *bz = b->bz;
     if (items) *items = b->total_items;
     if (blocks) *blocks = b->persistent_blocks;
     return JACOBI_OK;
@@ -401,7 +424,7 @@ int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scra
     }
     double lups = 0.0;
     for (const BatchGrid &G : b->grids) lups += (double)G.nx * G.ny * G.nz * G.T;
-    const int tiles[][2] = {{32, 4}, {32, 8}, {32, 16}, {64, 4}, {64, 8}, {128, 2}, {128, 4}};
+    const int tiles[][3] = {{32, 4, 0}, {32, 8, 0}, {32, 16, 0}, {64, 4, 0}, {64, 8, 0}, {128, 2, 0}, {32, 8, 64}};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return JACOBI_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -409,9 +432,9 @@ int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scra
         return JACOBI_ERR_CUDA;
     }
     double best = -1.0;
-    int bbx = b->bx, bby = b->by, st = JACOBI_OK;
+    int bbx = b->bx, bby = b->by, bbz = b->bz, st = JACOBI_OK;
     for (const auto &t : tiles) {
-        st = jacobi_batch_set_tile(b, t[0], t[1]);
+        st = jacobi_batch_set_tile(b, t[0], t[1], t[2]);
         if (st != JACOBI_OK) break;
         st = jacobi_batch_run(b, scratchA, scratchB, stream);  // warm-up
         if (st != JACOBI_OK) break;
@@ -430,13 +453,14 @@ int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scra
             best = g;
             bbx = t[0];
             bby = t[1];
+            bbz = t[2];
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != JACOBI_OK) return st;
     if (glups) *glups = best;
-    return jacobi_batch_set_tile(b, bbx, bby);
+    return jacobi_batch_set_tile(b, bbx, bby, bbz);
 }
 
 }  // extern "C"

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "jacobi.h"
 
 namespace jac {
@@ -61,3 +63,30 @@ cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, 
 int plan_passes(int T, int d, int *depths, int max_passes);
 
 }  // namespace jac
+
+// Library-owned state behind a jacobi_h.
+struct jacobi_plan_s {
+    int nx = 0, ny = 0, nz = 0, dtype = 0, device = 0, sms = 0;
+    jac::Plan plan;
+    bool forced = false;
+    int *d_status = nullptr;
+    int fault_mode = 0;
+    unsigned long long limit_ns = 2000000000ull;
+    void *hostA = nullptr, *hostB = nullptr;  // device grids of jacobi_sweep_host
+    bool prof = false;                          // profiling of pass launches
+    std::vector<cudaEvent_t> ev_pool;           // events, reused after a read
+    size_t ev_used = 0;
+    int prof_pass = 0, prof_other = 0;
+    // Poisson / refinement scratch (allocated on first use, freed by destroy)
+    void *g = nullptr;          // source term h^2 r (FP32) or h^2 f (FP64)
+    void *e0 = nullptr, *e1 = nullptr;  // FP32 correction grids
+    double *partials = nullptr;  // per-block partial sums of squares
+    double *h_sum = nullptr;     // pinned host mirror of one reduced sum
+    jacobi_batch_h inner = nullptr;  // one-grid persistent sweep engine
+    int inner_dtype = -1, inner_T = -1;
+};
+
+namespace jac {
+void free_poisson_scratch(jacobi_plan_s *h);
+}
+

@@ -1,0 +1,277 @@
+// Poisson problem -Lap_h u = f (7-point Laplacian, Dirichlet halo) on top of
+// the Jacobi sweeps:
+//   jacobi_poisson_residual  r = f - A_h u and ||r||/||f|| in FP64
+//   jacobi_poisson_jacobi    plain FP64 Jacobi with source term h^2 f
+//   jacobi_refine            mixed-precision iterative refinement: FP64
+//                            residual and update, FP32 inner Jacobi sweeps on
+//                            the correction
+// The inner sweeps (and the plain FP64 Jacobi) run on the persistent batch
+// engine with one grid: hundreds of dependent sweeps of a small grid in one
+// launch, each tile waiting only on its neighbours (no launch per sweep).
+// Sums of squares are reduced in a fixed order (per-thread grid-stride
+// order, then a fixed tree per block, then the block partials in index
+// order), so results do not depend on timing.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "jacobi_internal.h"
+
+namespace jac {
+namespace {
+
+constexpr int kRedBlocks = 304;  // fixed reduction layout (2 x 152 SMs)
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double sh[kRedThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kRedThreads / 32; ++w) t = __dadd_rn(t, sh[w]);
+    return t;
+}
+
+// Interior cell c (0 <= c < nx*ny*nz, x fastest) -> array index.
+__device__ __forceinline__ long long cell_index(long long c, int nx, int ny)
+{
+    const long long x = c % nx, y = (c / nx) % ny, z = c / ((long long)nx * ny);
+    return ((z + 1) * (ny + 2) + (y + 1)) * (long long)(nx + 2) + (x + 1);
+}
+
+// partials[b] = sum of f^2 over the cells of block b.
+__global__ void __launch_bounds__(kRedThreads) sumsq_kernel(const double *f, int nx, int ny, int nz,
+                                                            double *partials)
+{
+    const long long n = (long long)nx * ny * nz;
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)kRedThreads + threadIdx.x; c < n; c += (long long)kRedBlocks * kRedThreads) {
+        const double v = f[cell_index(c, nx, ny)];
+        acc = __fma_rn(v, v, acc);
+    }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// r = f - A_h u (A_h u = (6u - neighbour sum, order of Eq. 1) / h^2, the
+// division replaced by the product with 1/h^2); optionally writes the
+// source term of the correction, g = RN_f32(h^2 r); partial sums of r^2.
+__global__ void __launch_bounds__(kRedThreads) residual_kernel(const double *u, const double *f, float *g, int nx,
+                                                               int ny, int nz, double h2, double inv_h2,
+                                                               double *partials)
+{
+    const long long n = (long long)nx * ny * nz;
+    const long long NXP = nx + 2, plane = NXP * (ny + 2);
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)kRedThreads + threadIdx.x; c < n; c += (long long)kRedBlocks * kRedThreads) {
+        const long long i = cell_index(c, nx, ny);
+        double s = __dadd_rn(u[i - 1], u[i + 1]);
+        s = __dadd_rn(s, u[i - NXP]);
+        s = __dadd_rn(s, u[i + NXP]);
+        s = __dadd_rn(s, u[i - plane]);
+        s = __dadd_rn(s, u[i + plane]);
+        const double au = __dmul_rn(__dsub_rn(__dmul_rn(6.0, u[i]), s), inv_h2);
+        const double r = __dsub_rn(f[i], au);
+        if (g) g[i] = __double2float_rn(__dmul_rn(h2, r));
+        acc = __fma_rn(r, r, acc);
+    }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void reduce_partials_kernel(const double *partials, int n, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < n; ++b) t = __dadd_rn(t, partials[b]);
+        *out = t;
+    }
+}
+
+// u += (double) e on the interior.
+__global__ void update_kernel(double *u, const float *e, int nx, int ny, int nz)
+{
+    const long long n = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const long long i = cell_index(c, nx, ny);
+        u[i] = __dadd_rn(u[i], (double)e[i]);
+    }
+}
+
+// g = h^2 f (FP64) on the interior.
+__global__ void scale_kernel(const double *f, double *g, double h2, int nx, int ny, int nz)
+{
+    const long long n = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const long long i = cell_index(c, nx, ny);
+        g[i] = __dmul_rn(h2, f[i]);
+    }
+}
+
+size_t cells(const jacobi_plan_s *h) { return (size_t)(h->nx + 2) * (h->ny + 2) * (size_t)(h->nz + 2); }
+
+int ensure_common(jacobi_plan_s *h)
+{
+    if (!h->partials && cudaMalloc(&h->partials, sizeof(double) * (kRedBlocks + 1)) != cudaSuccess)
+        return JACOBI_ERR_ALLOC;
+    if (!h->h_sum && cudaMallocHost(&h->h_sum, sizeof(double)) != cudaSuccess) return JACOBI_ERR_ALLOC;
+    return JACOBI_OK;
+}
+
+// One-grid persistent engine with T sweeps of the given dtype on this grid.
+int ensure_inner(jacobi_plan_s *h, int dtype, int T)
+{
+    if (h->inner && h->inner_dtype == dtype && h->inner_T == T) return JACOBI_OK;
+    if (h->inner) jacobi_batch_destroy(h->inner);
+    h->inner = nullptr;
+    int st = jacobi_batch_create(&h->inner, 1, &h->nx, &h->ny, &h->nz, &dtype, &T);
+    if (st != JACOBI_OK) return st;
+    // small grid, many dependent sweeps: short tiles split in z give every
+    // SM work in each sweep
+    const long long cells_xy = (long long)h->nx * h->ny;
+    int bz = 0;
+    if (cells_xy * h->nz < (1ll << 24)) bz = 16;
+    st = jacobi_batch_set_tile(h->inner, 32, 4, bz);
+    if (st != JACOBI_OK) return st;
+    h->inner_dtype = dtype;
+    h->inner_T = T;
+    return JACOBI_OK;
+}
+
+// sqrt of the reduced sum of squares, read back to the host.
+int read_norm(jacobi_plan_s *h, cudaStream_t s, double *out)
+{
+    reduce_partials_kernel<<<1, 32, 0, s>>>(h->partials, kRedBlocks, h->partials + kRedBlocks);
+    cudaError_t e = cudaMemcpyAsync(h->h_sum, h->partials + kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return JACOBI_ERR_CUDA;
+    *out = std::sqrt(*h->h_sum);
+    return JACOBI_OK;
+}
+
+int residual_norm(jacobi_plan_s *h, const double *u, const double *f, float *g, double hgrid, cudaStream_t s,
+                  double *rnorm)
+{
+    const double h2 = hgrid * hgrid;
+    residual_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(u, f, g, h->nx, h->ny, h->nz, h2, 1.0 / h2, h->partials);
+    if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
+    return read_norm(h, s, rnorm);
+}
+
+int f_norm(jacobi_plan_s *h, const double *f, cudaStream_t s, double *fnorm)
+{
+    sumsq_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(f, h->nx, h->ny, h->nz, h->partials);
+    if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
+    return read_norm(h, s, fnorm);
+}
+
+}  // namespace
+
+void free_poisson_scratch(jacobi_plan_s *h)
+{
+    if (h->g) cudaFree(h->g);
+    if (h->e0) cudaFree(h->e0);
+    if (h->e1) cudaFree(h->e1);
+    if (h->partials) cudaFree(h->partials);
+    if (h->h_sum) cudaFreeHost(h->h_sum);
+    if (h->inner) jacobi_batch_destroy(h->inner);
+    h->g = h->e0 = h->e1 = nullptr;
+    h->partials = nullptr;
+    h->h_sum = nullptr;
+    h->inner = nullptr;
+}
+
+}  // namespace jac
+
+using namespace jac;
+
+extern "C" {
+
+int jacobi_poisson_residual(jacobi_h h, const void *u, const void *f, double hgrid, jacobi_stream_t stream,
+                            double *rel)
+{
+    if (!h || !u || !f || !rel || !(hgrid > 0.0)) return JACOBI_ERR_ARG;
+    if (h->dtype != JACOBI_F64) return JACOBI_ERR_DTYPE;
+    int st = ensure_common(h);
+    if (st != JACOBI_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double fn = 0.0, rn = 0.0;
+    st = f_norm(h, static_cast<const double *>(f), s, &fn);
+    if (st == JACOBI_OK) st = residual_norm(h, static_cast<const double *>(u), static_cast<const double *>(f), nullptr,
+                                            hgrid, s, &rn);
+    if (st != JACOBI_OK) return st;
+    *rel = (fn > 0.0) ? rn / fn : 0.0;
+    return JACOBI_OK;
+}
+
+int jacobi_poisson_jacobi(jacobi_h h, void *u, void *tmp, const void *f, double hgrid, int sweeps,
+                          jacobi_stream_t stream)
+{
+    if (!h || !u || !tmp || !f || u == tmp || sweeps < 0 || !(hgrid > 0.0)) return JACOBI_ERR_ARG;
+    if (h->dtype != JACOBI_F64) return JACOBI_ERR_DTYPE;
+    if (sweeps == 0) return JACOBI_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!h->g && cudaMalloc(&h->g, cells(h) * sizeof(double)) != cudaSuccess) return JACOBI_ERR_ALLOC;
+    int st = ensure_inner(h, JACOBI_F64, sweeps);
+    if (st != JACOBI_OK) return st;
+    scale_kernel<<<608, 256, 0, s>>>(static_cast<const double *>(f), static_cast<double *>(h->g), hgrid * hgrid,
+                                     h->nx, h->ny, h->nz);
+    if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
+    void *A[1] = {u}, *B[1] = {tmp};
+    const void *G[1] = {h->g};
+    return jacobi_batch_run_rhs(h->inner, A, B, G, stream);
+}
+
+int jacobi_refine(jacobi_h h, double *u, const double *f, double hgrid, double rel_tol, int inner_sweeps,
+                  int max_outer, jacobi_stream_t stream, int *outer_done, double *final_rel_residual)
+{
+    if (!h || !u || !f || !(hgrid > 0.0) || !(rel_tol >= 0.0) || inner_sweeps < 1 || max_outer < 0)
+        return JACOBI_ERR_ARG;
+    if (h->dtype != JACOBI_F64) return JACOBI_ERR_DTYPE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = ensure_common(h);
+    if (st != JACOBI_OK) return st;
+    const size_t n = cells(h);
+    // h->g holds either FP32 h^2 r (here) or FP64 h^2 f (plain solver); it
+    // is sized for FP64 and rewritten before every use
+    if (!h->g && cudaMalloc(&h->g, n * sizeof(double)) != cudaSuccess) return JACOBI_ERR_ALLOC;
+    if (!h->e0 && cudaMalloc(&h->e0, n * sizeof(float)) != cudaSuccess) return JACOBI_ERR_ALLOC;
+    if (!h->e1 && cudaMalloc(&h->e1, n * sizeof(float)) != cudaSuccess) return JACOBI_ERR_ALLOC;
+    st = ensure_inner(h, JACOBI_F32, inner_sweeps);
+    if (st != JACOBI_OK) return st;
+
+    double fn = 0.0;
+    st = f_norm(h, f, s, &fn);
+    if (st != JACOBI_OK) return st;
+    int outer = 0;
+    double rel = 0.0;
+    for (;;) {
+        double rn = 0.0;
+        st = residual_norm(h, u, f, static_cast<float *>(h->g), hgrid, s, &rn);
+        if (st != JACOBI_OK) return st;
+        rel = (fn > 0.0) ? rn / fn : 0.0;
+        if (rel <= rel_tol || outer >= max_outer) break;
+        if (cudaMemsetAsync(h->e0, 0, n * sizeof(float), s) != cudaSuccess) return JACOBI_ERR_CUDA;
+        if (cudaMemsetAsync(h->e1, 0, n * sizeof(float), s) != cudaSuccess) return JACOBI_ERR_CUDA;
+        void *A[1] = {h->e0}, *B[1] = {h->e1};
+        const void *G[1] = {h->g};
+        st = jacobi_batch_run_rhs(h->inner, A, B, G, stream);
+        if (st != JACOBI_OK) return st;
+        const float *e = static_cast<const float *>((inner_sweeps % 2 == 0) ? h->e0 : h->e1);
+        update_kernel<<<608, 256, 0, s>>>(u, e, h->nx, h->ny, h->nz);
+        if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
+        ++outer;
+    }
+    int dev_status = 0;
+    st = jacobi_batch_get_status(h->inner, &dev_status);
+    if (st != JACOBI_OK) return st;
+    if (dev_status != 0) return dev_status;
+    if (outer_done) *outer_done = outer;
+    if (final_rel_residual) *final_rel_residual = rel;
+    return rel <= rel_tol ? JACOBI_OK : JACOBI_ERR_NOT_CONVERGED;
+}
+
+}  // extern "C"

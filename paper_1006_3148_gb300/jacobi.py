@@ -70,12 +70,16 @@ def load(build_if_missing: bool = True):
             "jacobi_debug_set_fault": ([P, i, i], i),
             "jacobi_plan_passes": ([i, i, pi, i], i),
             "jacobi_profile_enable": ([P, i], i),
+            "jacobi_poisson_residual": ([P, P, P, d, P, ctypes.POINTER(d)], i),
+            "jacobi_poisson_jacobi": ([P, P, P, P, d, i, P], i),
+            "jacobi_refine": ([P, P, P, d, d, i, i, P, pi, ctypes.POINTER(d)], i),
             "jacobi_batch_create": ([ctypes.POINTER(P), i, pi, pi, pi, pi, pi], i),
             "jacobi_batch_run": ([P, ctypes.POINTER(P), ctypes.POINTER(P), P], i),
             "jacobi_batch_destroy": ([P], i),
-            "jacobi_batch_set_tile": ([P, i, i], i),
+            "jacobi_batch_set_tile": ([P, i, i, i], i),
+            "jacobi_batch_run_rhs": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P], i),
             "jacobi_batch_tune": ([P, ctypes.POINTER(P), ctypes.POINTER(P), P, ctypes.POINTER(d)], i),
-            "jacobi_batch_get_info": ([P, pi, pi, ctypes.POINTER(ctypes.c_longlong), pi], i),
+            "jacobi_batch_get_info": ([P, pi, pi, pi, ctypes.POINTER(ctypes.c_longlong), pi], i),
             "jacobi_batch_get_status": ([P, pi], i),
             "jacobi_batch_debug_set_fault": ([P, i, i], i),
             "jacobi_check_division": ([ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong),
@@ -295,8 +299,17 @@ def jacobi_batch_destroy(b: Batch):
     b.close()
 
 
-def jacobi_batch_set_tile(b: Batch, bx: int, by: int):
-    _check(load().jacobi_batch_set_tile(b.ptr, int(bx), int(by)), "jacobi_batch_set_tile")
+def jacobi_batch_set_tile(b: Batch, bx: int, by: int, bz: int = 0):
+    _check(load().jacobi_batch_set_tile(b.ptr, int(bx), int(by), int(bz)), "jacobi_batch_set_tile")
+
+
+def jacobi_batch_run_rhs(b: Batch, A, B, RHS, stream=None):
+    """Poisson form: grid g uses the source term RHS[g] (= h^2 f, or None)."""
+    pa, pb = b._ptrs(A), b._ptrs(B)
+    pr = (ctypes.c_void_p * b.n)(*[None if r is None else _grid_ptr(r, b.shape(g), b.dtypes[g]).value
+                                   for g, r in enumerate(RHS)])
+    _check(load().jacobi_batch_run_rhs(b.ptr, pa, pb, pr, _stream(stream)), "jacobi_batch_run_rhs")
+    return [B[g] if b.Ts[g] % 2 == 1 else A[g] for g in range(b.n)]
 
 
 def jacobi_batch_tune(b: Batch, scratchA, scratchB, stream=None) -> float:
@@ -307,10 +320,10 @@ def jacobi_batch_tune(b: Batch, scratchA, scratchB, stream=None) -> float:
 
 
 def jacobi_batch_get_info(b: Batch) -> dict:
-    bx, by, blocks, items = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
-    _check(load().jacobi_batch_get_info(b.ptr, ctypes.byref(bx), ctypes.byref(by), ctypes.byref(items),
-                                        ctypes.byref(blocks)), "jacobi_batch_get_info")
-    return {"bx": bx.value, "by": by.value, "items": items.value, "blocks": blocks.value}
+    bx, by, bz, blocks, items = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _check(load().jacobi_batch_get_info(b.ptr, ctypes.byref(bx), ctypes.byref(by), ctypes.byref(bz),
+                                        ctypes.byref(items), ctypes.byref(blocks)), "jacobi_batch_get_info")
+    return {"bx": bx.value, "by": by.value, "bz": bz.value, "items": items.value, "blocks": blocks.value}
 
 
 def jacobi_batch_get_status(b: Batch) -> int:
@@ -321,3 +334,30 @@ def jacobi_batch_get_status(b: Batch) -> int:
 
 def jacobi_batch_debug_set_fault(b: Batch, mode: int, limit_ms: int = 2000):
     _check(load().jacobi_batch_debug_set_fault(b.ptr, int(mode), int(limit_ms)), "jacobi_batch_debug_set_fault")
+
+
+def jacobi_poisson_residual(h: Handle, u: torch.Tensor, f: torch.Tensor, hgrid: float, stream=None) -> float:
+    rel = ctypes.c_double()
+    _check(load().jacobi_poisson_residual(h.ptr, _grid_ptr(u, h.shape, h.dtype), _grid_ptr(f, h.shape, h.dtype),
+                                          float(hgrid), _stream(stream), ctypes.byref(rel)), "jacobi_poisson_residual")
+    return rel.value
+
+
+def jacobi_poisson_jacobi(h: Handle, u: torch.Tensor, tmp: torch.Tensor, f: torch.Tensor, hgrid: float,
+                          sweeps: int, stream=None) -> torch.Tensor:
+    _check(load().jacobi_poisson_jacobi(h.ptr, _grid_ptr(u, h.shape, h.dtype), _grid_ptr(tmp, h.shape, h.dtype),
+                                        _grid_ptr(f, h.shape, h.dtype), float(hgrid), int(sweeps), _stream(stream)),
+           "jacobi_poisson_jacobi")
+    return tmp if sweeps % 2 == 1 else u
+
+
+def jacobi_refine(h: Handle, u: torch.Tensor, f: torch.Tensor, hgrid: float, rel_tol: float, inner_sweeps: int,
+                  max_outer: int, stream=None):
+    """Returns (status, outer_done, final_rel); status 0 or -7 (not converged)."""
+    od, fr = ctypes.c_int(), ctypes.c_double()
+    st = load().jacobi_refine(h.ptr, _grid_ptr(u, h.shape, h.dtype), _grid_ptr(f, h.shape, h.dtype), float(hgrid),
+                              float(rel_tol), int(inner_sweeps), int(max_outer), _stream(stream), ctypes.byref(od),
+                              ctypes.byref(fr))
+    if st not in (0, -7):
+        raise JacobiError(st, "jacobi_refine")
+    return st, od.value, fr.value

@@ -42,7 +42,7 @@ def test_small_mixed_batch_all_tiles():
     Ts = [int(v) for v in rng.integers(0, 8, size=n)]
     hosts = _make(dims, f32, 40)
     b = J.Batch(dims, [torch.float32 if f else torch.float64 for f in f32], Ts)
-    for tile in [(32, 8), (4, 2), (1, 1), (64, 4), (7, 3)]:
+    for tile in [(32, 8), (4, 2), (1, 1), (64, 4), (7, 3), (8, 4, 3), (16, 2, 1)]:
         J.jacobi_batch_set_tile(b, *tile)
         _check(b, hosts, Ts)
     b.close()
@@ -81,5 +81,5 @@ def test_batch_workload_256_grids_32_to_192():
     hosts = _make(dims, f32, 1000)
     b = J.Batch(dims, [torch.float32 if f else torch.float64 for f in f32], Ts)
     info = J.jacobi_batch_get_info(b)
-    assert info["items"] > 0 and info["blocks"] > 0
+    assert info["items"] > 0 and info["blocks"] > 0 and info["bz"] == 0
     _check(b, hosts, Ts)

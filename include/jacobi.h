@@ -201,6 +201,31 @@ int jacobi_refine(jacobi_h h, double *u, const double *f, double hgrid, double r
                   int inner_sweeps, int max_outer, jacobi_stream_t stream, int *outer_done,
                   double *final_rel_residual);
 
+/* Largest nz accepted by jacobi_poisson_residual_noalloc (its scratch holds
+ * two partial sums per z-plane plus two totals: 2*16384+2 doubles, 256 KB,
+ * held on every GPU that loads this library until the process exits). */
+#define JACOBI_NOALLOC_MAX_NZ 16384
+
+/* The relative residual ||f - A_h u||_2 / ||f||_2 of jacobi_poisson_residual
+ * (same operator and arithmetic, sums reduced per z-plane, so the last bits
+ * may differ), computed without allocating anything: no cudaMalloc, no
+ * cudaFree, no allocating library call, and no handle.  The paper has no
+ * counterpart; this exists for callers that cannot allocate device memory --
+ * code whose device memory is owned entirely by another allocator (a
+ * framework's caching pool, a fixed memory budget) and code on a
+ * latency-critical path where an allocation's implicit device
+ * synchronisation, or its failure under memory pressure, is not acceptable.
+ * Its scratch is a fixed device array inside the library (size: see
+ * JACOBI_NOALLOC_MAX_NZ); nz > JACOBI_NOALLOC_MAX_NZ returns JACOBI_ERR_ARG.
+ * u, f: device grids of interior nx*ny*nz as in jacobi_create; the result
+ * is read back, so the call synchronises stream.  The first call on a
+ * device looks up the array's device address (once per device, with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the one array: calls that overlap on the GPU (several streams
+ * or threads at once) race and must be serialised by the caller. */
+int jacobi_poisson_residual_noalloc(const void *u, const void *f, int nx, int ny, int nz,
+                                    double hgrid, jacobi_stream_t stream, double *rel);
+
 /* ---------------------------------------------------------------- batch
  * Many independent grids (each its own size, element type and sweep count
  * T_g) swept in ONE persistent kernel launch that a CUDA graph replays.

@@ -72,6 +72,7 @@ def load(build_if_missing: bool = True):
             "jacobi_profile_enable": ([P, i], i),
             "jacobi_poisson_residual": ([P, P, P, d, P, ctypes.POINTER(d)], i),
             "jacobi_poisson_jacobi": ([P, P, P, P, d, i, P], i),
+            "jacobi_poisson_residual_noalloc": ([P, P, i, i, i, d, P, ctypes.POINTER(d)], i),
             "jacobi_refine": ([P, P, P, d, d, i, i, P, pi, ctypes.POINTER(d)], i),
             "jacobi_batch_create": ([ctypes.POINTER(P), i, pi, pi, pi, pi, pi], i),
             "jacobi_batch_run": ([P, ctypes.POINTER(P), ctypes.POINTER(P), P], i),
@@ -361,3 +362,16 @@ def jacobi_refine(h: Handle, u: torch.Tensor, f: torch.Tensor, hgrid: float, rel
     if st not in (0, -7):
         raise JacobiError(st, "jacobi_refine")
     return st, od.value, fr.value
+
+
+def jacobi_poisson_residual_noalloc(u: torch.Tensor, f: torch.Tensor, hgrid: float, stream=None) -> float:
+    """Relative residual without any device allocation (library-internal
+    fixed scratch; nz <= JACOBI_NOALLOC_MAX_NZ; calls must not overlap)."""
+    nz, ny, nx = (s - 2 for s in u.shape)
+    shape = tuple(u.shape)
+    rel = ctypes.c_double()
+    _check(load().jacobi_poisson_residual_noalloc(_grid_ptr(u, shape, torch.float64),
+                                                  _grid_ptr(f, shape, torch.float64), nx, ny, nz, float(hgrid),
+                                                  _stream(stream), ctypes.byref(rel)),
+           "jacobi_poisson_residual_noalloc")
+    return rel.value

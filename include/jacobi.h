@@ -106,18 +106,21 @@ int jacobi_sweep_host(jacobi_h h, const void *A_host, void *out_host, int T,
 
 /* Forces a plan: kernel (JACOBI_KERNEL_*), temporal depth (1..16; 1 for
  * PLAIN), tile interior bx*by (bx, by >= 1), z chunk bz >= 1 interior
- * planes per cluster, and ring = plane slots between two pipeline levels
- * (4, 8 or 16; 0 = the deepest that fits 100 KB of shared memory).  The
+ * planes per cluster, ring = plane slots between two pipeline levels
+ * (4, 8 or 16; 0 = the deepest that fits 100 KB of shared memory), and
+ * threads = CTA width (128, 256 or 512; 0 = automatic).  The
  * ring depth is the pipeline looseness of Sect. 2.2 (a producer may run up
  * to ring planes ahead of its consumer; at least one plane, Eq. 3).
- * bz and ring are ignored by PLAIN.  Depths > 8 need the non-portable
+ * bz, ring and threads are ignored by PLAIN.  Depths > 8 need the non-portable
  * cluster size.  JACOBI_KERNEL_AUTO returns to the tuned/default plan.
  * Returns JACOBI_ERR_UNSUPPORTED if the plan cannot launch on this device
  * (shared memory, registers, cluster occupancy). */
-int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, int ring);
+int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, int ring,
+                    int threads);
 
-/* Reads back the plan jacobi_sweep will use (ring 0 = automatic). */
-int jacobi_get_plan(jacobi_h h, int *kernel, int *depth, int *bx, int *by, int *bz, int *ring);
+/* Reads back the plan jacobi_sweep will use (ring/threads 0 = automatic). */
+int jacobi_get_plan(jacobi_h h, int *kernel, int *depth, int *bx, int *by, int *bz, int *ring,
+                    int *threads);
 
 /* Autotuner (experiment-driven parameter choice, Sect. 2.4): fills the
  * caller's scratch grids (same size as the handle's grids; contents

@@ -88,8 +88,9 @@ int check_plan(const jacobi_plan_s *h, const Plan &p)
     if (p.kernel != JACOBI_KERNEL_TB) return JACOBI_ERR_ARG;
     if (p.depth < 1 || p.depth > 16 || p.bx < 1 || p.by < 1 || p.bz < 1) return JACOBI_ERR_ARG;
     if (p.ring != 0 && p.ring != 4 && p.ring != 8 && p.ring != 16) return JACOBI_ERR_ARG;
+    if (p.threads != 0 && p.threads != 128 && p.threads != 256 && p.threads != 512) return JACOBI_ERR_ARG;
     TbLaunch L;
-    if (tb_configure(h->dtype, p.depth, p.bx, p.by, p.ring, &L) != cudaSuccess) return JACOBI_ERR_UNSUPPORTED;
+    if (tb_configure(h->dtype, p.depth, p.bx, p.by, p.ring, p.threads, &L) != cudaSuccess) return JACOBI_ERR_UNSUPPORTED;
     int clusters = 0;
     cudaError_t e = tb_max_clusters(h->dtype, L, p.depth, &clusters);
     if (e != cudaSuccess) {
@@ -140,7 +141,7 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
     int Ldepth = -1;
     for (int q = 0; q < P; ++q) {
         if (depths[q] != Ldepth) {
-            if (tb_configure(h->dtype, depths[q], p.bx, p.by, p.ring, &L) != cudaSuccess) return JACOBI_ERR_UNSUPPORTED;
+            if (tb_configure(h->dtype, depths[q], p.bx, p.by, p.ring, p.threads, &L) != cudaSuccess) return JACOBI_ERR_UNSUPPORTED;
             Ldepth = depths[q];
         }
         a.depth = depths[q];
@@ -276,7 +277,7 @@ int jacobi_sweep_host(jacobi_h h, const void *A_host, void *out_host, int T, jac
     return JACOBI_OK;
 }
 
-int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, int ring)
+int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, int ring, int threads)
 {
     if (!h) return JACOBI_ERR_ARG;
     if (kernel == JACOBI_KERNEL_AUTO) {
@@ -290,6 +291,7 @@ int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, i
     p.by = by;
     p.bz = bz;
     p.ring = (kernel == JACOBI_KERNEL_PLAIN) ? 0 : ring;
+    p.threads = (kernel == JACOBI_KERNEL_PLAIN) ? 0 : threads;
     const int st = check_plan(h, p);
     if (st != JACOBI_OK) return st;
     h->plan = p;
@@ -297,7 +299,7 @@ int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, i
     return JACOBI_OK;
 }
 
-int jacobi_get_plan(jacobi_h h, int *kernel, int *depth, int *bx, int *by, int *bz, int *ring)
+int jacobi_get_plan(jacobi_h h, int *kernel, int *depth, int *bx, int *by, int *bz, int *ring, int *threads)
 {
     if (!h) return JACOBI_ERR_ARG;
     const Plan p = active_plan(h);
@@ -307,6 +309,7 @@ int jacobi_get_plan(jacobi_h h, int *kernel, int *depth, int *bx, int *by, int *
     if (by) *by = p.by;
     if (bz) *bz = p.bz;
     if (ring) *ring = p.ring;
+    if (threads) *threads = p.threads;
     return JACOBI_OK;
 }
 
@@ -411,6 +414,7 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
     const int tiles[][2] = {{32, 16}, {64, 8}, {64, 16}, {32, 32}, {64, 32}, {128, 16}, {128, 32}, {64, 64}};
     const int bzs[] = {32, 64, 128, 256};
     const int rings[] = {4, 8, 16};
+    const int widths[] = {0, 128, 256, 512};
     auto clampp = [&](Plan p) {
         if (p.bx > h->nx) p.bx = h->nx;
         if (p.by > h->ny) p.by = h->ny;
@@ -474,6 +478,12 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
                 p.ring = rg;
                 consider(clampp(p));
             }
+        const Plan base2 = bestp;
+        for (int w : widths) {
+            Plan p = base2;
+            p.threads = w;
+            consider(clampp(p));
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

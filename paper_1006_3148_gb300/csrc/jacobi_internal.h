@@ -38,7 +38,8 @@ struct Plan {
     int kernel = JACOBI_KERNEL_TB;
     int depth = 1;
     int bx = 64, by = 16, bz = 64;
-    int ring = 0;  // ring slots per CTA (4, 8, 16); 0 = largest that fits the budget
+    int ring = 0;     // ring slots per CTA (4, 8, 16); 0 = largest that fits the budget
+    int threads = 0;  // threads per CTA (128, 256, 512); 0 = automatic
 };
 
 // Launch resources of a TB plan (host side), filled by tb_configure.
@@ -51,7 +52,7 @@ struct TbLaunch {
 
 
 // Kernels (sweep_kernels.cu).  All return cudaError_t of the launch.
-cudaError_t tb_configure(int dtype, int depth, int bx, int by, int ring, TbLaunch *out);
+cudaError_t tb_configure(int dtype, int depth, int bx, int by, int ring, int threads, TbLaunch *out);
 cudaError_t tb_launch(int dtype, const TbArgs &a, const TbLaunch &L, cudaStream_t s);
 cudaError_t tb_max_clusters(int dtype, const TbLaunch &L, int depth, int *clusters);
 cudaError_t plain_launch(int dtype, const PlainArgs &a, cudaStream_t s);

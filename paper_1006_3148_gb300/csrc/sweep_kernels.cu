@@ -416,11 +416,15 @@ __global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_
                 st_async_v(out_base + (uint32_t)goff[q] * (uint32_t)sizeof(T), v, out_bar);
             } else {
                 T *gpo = drow + gofs[q];
-                if ((f & (((1u << VEC) - 1u) << 8)) == (((1u << VEC) - 1u) << 8) && cs == VEC) {
+                const bool full = (f & (((1u << VEC) - 1u) << 8)) == (((1u << VEC) - 1u) << 8);
+                if (full && cs == VEC) {
                     V t;
                     if constexpr (VEC == 4) t = make_float4(v[0], v[1], v[2], v[3]);
                     else t = make_double2(v[0], v[1]);
                     *reinterpret_cast<V *>(gpo) = t;
+                } else if (VEC == 4 && full && cs == 2) {
+                    reinterpret_cast<float2 *>(gpo)[0] = make_float2((float)v[0], (float)v[1]);
+                    reinterpret_cast<float2 *>(gpo)[1] = make_float2((float)v[2], (float)v[3]);
                 } else {
 #pragma unroll
                     for (int l = 0; l < VEC; ++l)
@@ -449,7 +453,7 @@ struct Variant {
 constexpr size_t kRingBudget = 100 * 1024;  // auto ring depth: fit 2 CTAs per SM
 // Preferred order: the widest CTA whose threads cover the level-1 groups
 // (more warps per SM hide the latency of the per-plane pipeline).
-constexpr Variant kVariants[] = {{512, 1}, {512, 2}, {256, 2}, {256, 4}, {128, 8}, {256, 6}, {128, 4}, {128, 2}, {128, 6}};
+constexpr Variant kVariants[] = {{512, 1}, {512, 2}, {256, 1}, {256, 2}, {256, 4}, {256, 6}, {128, 2}, {128, 4}, {128, 6}, {128, 8}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kSmemMax = 232448;  // 227 KB per CTA on sm_100-class GPUs
 
@@ -459,6 +463,7 @@ template <typename T>
 const void *tb_kernel_ptr(int nc, int maxg)
 {
     if (nc == 512 && maxg == 1) return (const void *)tb_pass_kernel<T, 512, 1, 4>;
+    if (nc == 256 && maxg == 1) return (const void *)tb_pass_kernel<T, 256, 1, 8>;
     if (nc == 512 && maxg == 2) return (const void *)tb_pass_kernel<T, 512, 2, 4>;
     if (nc == 128 && maxg == 2) return (const void *)tb_pass_kernel<T, 128, 2, 16>;
     if (nc == 128 && maxg == 4) return (const void *)tb_pass_kernel<T, 128, 4, 16>;
@@ -486,7 +491,7 @@ cudaError_t prepare(const void *fn)
 
 }  // namespace
 
-cudaError_t tb_configure(int dtype, int depth, int bx, int by, int ring, TbLaunch *out)
+cudaError_t tb_configure(int dtype, int depth, int bx, int by, int ring, int threads, TbLaunch *out)
 {
     const int es = dtype == JACOBI_F64 ? 8 : 4;
     const int V = 16 / es;
@@ -508,13 +513,31 @@ cudaError_t tb_configure(int dtype, int depth, int bx, int by, int ring, TbLaunc
     // groups of the widest output region (level 1): one extra group for the
     // alignment of its first column
     const long long groups = (long long)((bx + 2 * (depth - 1) + V - 1) / V + 1) * (by + 2 * (depth - 1));
+    // Automatic width: the fewest threads (up to 2 groups each) that cover
+    // the groups, else more groups per thread; a forced width takes the
+    // smallest group count per thread that covers the tile.
     L.nc = 0;
+    if (threads == 0) {
+        for (int nc : {128, 256, 512})
+            if ((long long)nc * 2 >= groups) {
+                threads = nc;
+                break;
+            }
+        if (threads == 0) threads = 512;
+    }
+    int best = 1 << 30;
     for (const Variant &v : kVariants)
-        if ((long long)v.nc * v.maxc >= groups) {
+        if (v.nc == threads && (long long)v.nc * v.maxc >= groups && v.maxc < best) {
             L.nc = v.nc;
             L.maxc = v.maxc;
-            break;
+            best = v.maxc;
         }
+    if (L.nc == 0)  // forced width too narrow for this tile: widest that fits
+        for (const Variant &v : kVariants)
+            if ((long long)v.nc * v.maxc >= groups && (L.nc == 0 || v.nc * v.maxc < L.nc * L.maxc)) {
+                L.nc = v.nc;
+                L.maxc = v.maxc;
+            }
     if (L.nc == 0 || L.smem > (size_t)kSmemMax) return cudaErrorInvalidConfiguration;
     *out = L;
     return cudaSuccess;

@@ -63,8 +63,8 @@ def load(build_if_missing: bool = True):
             "jacobi_destroy": ([P], i),
             "jacobi_sweep": ([P, P, P, i, P], i),
             "jacobi_sweep_host": ([P, P, P, i, P], i),
-            "jacobi_set_plan": ([P, i, i, i, i, i, i], i),
-            "jacobi_get_plan": ([P, pi, pi, pi, pi, pi, pi], i),
+            "jacobi_set_plan": ([P, i, i, i, i, i, i, i], i),
+            "jacobi_get_plan": ([P, pi, pi, pi, pi, pi, pi, pi], i),
             "jacobi_tune": ([P, P, P, P, ctypes.POINTER(d)], i),
             "jacobi_get_status": ([P, pi], i),
             "jacobi_debug_set_fault": ([P, i, i], i),
@@ -182,15 +182,15 @@ def jacobi_sweep_host(h: Handle, A_host: torch.Tensor, out_host: torch.Tensor, T
 
 
 def jacobi_set_plan(h: Handle, kernel: int, depth: int = 1, bx: int = 64, by: int = 16, bz: int = 64,
-                    ring: int = 0):
-    _check(load().jacobi_set_plan(h.ptr, int(kernel), int(depth), int(bx), int(by), int(bz), int(ring)),
-           "jacobi_set_plan")
+                    ring: int = 0, threads: int = 0):
+    _check(load().jacobi_set_plan(h.ptr, int(kernel), int(depth), int(bx), int(by), int(bz), int(ring),
+                                  int(threads)), "jacobi_set_plan")
 
 
 def jacobi_get_plan(h: Handle) -> dict:
-    v = [ctypes.c_int() for _ in range(6)]
+    v = [ctypes.c_int() for _ in range(7)]
     _check(load().jacobi_get_plan(h.ptr, *[ctypes.byref(x) for x in v]), "jacobi_get_plan")
-    return dict(zip(("kernel", "depth", "bx", "by", "bz", "ring"), (x.value for x in v)))
+    return dict(zip(("kernel", "depth", "bx", "by", "bz", "ring", "threads"), (x.value for x in v)))
 
 
 def jacobi_tune(h: Handle, scratchA: torch.Tensor, scratchB: torch.Tensor, stream=None) -> float:

@@ -59,11 +59,13 @@ PLANS = [
     (J.KERNEL_TB, 2, 8, 8, 8, 16),
     (J.KERNEL_TB, 4, 16, 8, 20, 4),
     (J.KERNEL_TB, 1, 32, 8, 16, 8),
+    (J.KERNEL_TB, 2, 16, 8, 8, 4, 128),
+    (J.KERNEL_TB, 3, 24, 12, 8, 8, 512),
 ]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("plan", PLANS, ids=lambda p: "k%d_d%d_%dx%dx%d" % p[:5] + ("_r%d" % p[5] if len(p) > 5 else ""))
+@pytest.mark.parametrize("plan", PLANS, ids=lambda p: "k%d_d%d_%dx%dx%d" % p[:5] + "".join("_%d" % v for v in p[5:]))
 def test_fp64_bit_exact_small(shape, plan):
     for T in (1, 2, 3, 7, 12):
         got = _gpu(shape, 11, torch.float64, T, plan)
@@ -119,10 +121,11 @@ def test_argument_errors():
     assert L.jacobi_sweep(h.ptr, pa, pa, 1, s) == -1
     assert L.jacobi_sweep(h.ptr, ctypes.c_void_p(A.data_ptr() + 8), pb, 1, s) == -8
     assert L.jacobi_sweep(h.ptr, pa, ctypes.c_void_p(A.data_ptr() + 16), 1, s) == -1
-    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 0, 8, 8, 8, 0) == -1
-    assert L.jacobi_set_plan(h.ptr, 9, 1, 8, 8, 8, 0) == -1
-    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 1, 8, 8, 8, 5) == -1
-    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 8, 512, 512, 8, 0) == -9
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 0, 8, 8, 8, 0, 0) == -1
+    assert L.jacobi_set_plan(h.ptr, 9, 1, 8, 8, 8, 0, 0) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 1, 8, 8, 8, 5, 0) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 1, 8, 8, 8, 4, 96) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 8, 512, 512, 8, 0, 0) == -9
 
 
 def test_bounded_wait_timeout_reports_status_and_context_survives():

@@ -149,6 +149,16 @@ int jacobi_plan_passes(int T, int depth, int *depths, int max_passes);
 int jacobi_check_division(unsigned long long count, unsigned long long seed,
                           unsigned long long *mismatches, unsigned long long *first_bad);
 
+/* Self-test of the exact FP64 addition that part of the FP64 sums use (the
+ * additions of Eq. 1 moved to the integer pipe): compares it bit for bit
+ * with the device's FP64 addition for 3*count pairs -- random bit patterns,
+ * and same-sign pairs whose exponents differ by 0..63 (carries, sticky
+ * bits, ties) -- from SplitMix64 stream `seed`.  Synchronises the device.
+ * *mismatches = differing results; first_bad[0..1] (may be NULL) = one
+ * failing pair. */
+int jacobi_check_addition(unsigned long long count, unsigned long long seed,
+                          unsigned long long *mismatches, unsigned long long *first_bad);
+
 /* Reads and clears the handle's device status word (synchronises the
  * device).  *device_status: 0 = fine, else the first JACOBI_ERR_* code a
  * kernel recorded (JACOBI_ERR_TIMEOUT, JACOBI_ERR_BOUNDS). */

@@ -52,8 +52,69 @@ __global__ void check_structured(unsigned long long *bad, unsigned long long *fi
     }
 }
 
+__device__ void check_add(unsigned long long ba, unsigned long long bb, unsigned long long *bad,
+                          unsigned long long *first)
+{
+    const double x = __longlong_as_double((long long)ba), y = __longlong_as_double((long long)bb);
+    const double r = add_rn_int(x, y), e = __dadd_rn(x, y);
+    if (r != r && e != e) return;  // both NaN
+    if (__double_as_longlong(r) != __double_as_longlong(e)) {
+        if (atomicAdd(bad, 1ull) == 0ull) {
+            first[0] = ba;
+            first[1] = bb;
+        }
+    }
+}
+
+// Random pairs: independent bit patterns, and pairs with the same sign and
+// exponents a random distance 0..63 apart (the fast path's cases: carries,
+// sticky bits, ties).
+__global__ void check_add_random(unsigned long long count, unsigned long long seed, unsigned long long *bad,
+                                 unsigned long long *first)
+{
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long r1 = splitmix64(seed + 3 * i * 0x9E3779B97F4A7C15ull);
+        const unsigned long long r2 = splitmix64(seed + (3 * i + 1) * 0x9E3779B97F4A7C15ull);
+        const unsigned long long r3 = splitmix64(seed + (3 * i + 2) * 0x9E3779B97F4A7C15ull);
+        check_add(r1, r2, bad, first);
+        const unsigned e1 = 1u + (unsigned)((r3 >> 8) % 2045u);
+        const unsigned d = (unsigned)(r3 & 63u);
+        const unsigned e2 = (e1 > d) ? e1 - d : 1u;
+        const unsigned long long s = (r3 >> 63) << 63;
+        const unsigned long long a = s | ((unsigned long long)e1 << 52) | (r1 & 0xFFFFFFFFFFFFFull);
+        unsigned long long b = s | ((unsigned long long)e2 << 52) | (r2 & 0xFFFFFFFFFFFFFull);
+        if ((r3 >> 20) & 1ull) b = (b & ~0xFFFFFFFFFull) | (1ull << ((r3 >> 21) % 36));  // sparse low bits: ties
+        check_add(a, b, bad, first);
+        check_add(b, a, bad, first);
+    }
+}
+
 }  // namespace
 }  // namespace jac
+
+extern "C" int jacobi_check_addition(unsigned long long count, unsigned long long seed,
+                                     unsigned long long *mismatches, unsigned long long *first_bad)
+{
+    if (!mismatches) return JACOBI_ERR_ARG;
+    unsigned long long *d = nullptr;
+    if (cudaMalloc(&d, 3 * sizeof(unsigned long long)) != cudaSuccess) return JACOBI_ERR_ALLOC;
+    cudaError_t e = cudaMemset(d, 0, 3 * sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+        jac::check_add_random<<<152 * 16, 256>>>(count, seed, d, d + 1);
+        e = cudaGetLastError();
+    }
+    unsigned long long h[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return JACOBI_ERR_CUDA;
+    *mismatches = h[0];
+    if (first_bad) {
+        first_bad[0] = h[1];
+        first_bad[1] = h[2];
+    }
+    return JACOBI_OK;
+}
 
 extern "C" int jacobi_check_division(unsigned long long count, unsigned long long seed,
                                      unsigned long long *mismatches, unsigned long long *first_bad)

@@ -22,6 +22,7 @@
 // neighbouring tile.
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "arith.cuh"
 #include "jacobi_internal.h"
@@ -80,21 +81,31 @@ __global__ void fill_kernel(T *p, long long n, T v)
 }
 
 // ----------------------------------------------------------------- plain
+// One sweep per launch.  Thread (i, j) walks kz planes of its column with the
+// values at k-1, k, k+1 in registers; the four in-plane neighbours come from
+// global memory (mostly L1 hits: neighbouring threads load them too).
 template <typename T>
 __global__ void __launch_bounds__(256) plain_pass_kernel(const PlainArgs a)
 {
-    const T *__restrict__ src = static_cast<const T *>(a.src);
-    T *__restrict__ dst = static_cast<T *>(a.dst);
     const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     if (i > a.nx || j > a.ny) return;
     const long long NXP = a.nx + 2, plane = NXP * (a.ny + 2);
     const int kb = 1 + blockIdx.z * a.kz;
     const int ke = min(kb + a.kz, a.nz + 1);
+    const long long c0 = kb * plane + j * NXP + i;
+    const T *__restrict__ p = static_cast<const T *>(a.src) + c0;
+    T *__restrict__ q = static_cast<T *>(a.dst) + c0;
+    const int nxp = a.nx + 2;
+    T lo = __ldg(p - plane), mid = __ldg(p);
+#pragma unroll 4
     for (int k = kb; k < ke; ++k) {
-        const long long c = k * plane + j * NXP + i;
-        dst[c] = Arith<T>::update(__ldg(src + c - 1), __ldg(src + c + 1), __ldg(src + c - NXP),
-                                  __ldg(src + c + NXP), __ldg(src + c - plane), __ldg(src + c + plane));
+        const T hi = __ldg(p + plane);
+        *q = Arith<T>::update(__ldg(p - 1), __ldg(p + 1), __ldg(p - nxp), __ldg(p + nxp), lo, hi);
+        lo = mid;
+        mid = hi;
+        p += plane;
+        q += plane;
     }
 }
 
@@ -348,16 +359,18 @@ __global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_
         }
     };
 
-    T av[MAXG][VEC], bv[MAXG][VEC];
+    // z queue: three register sets that take the roles (plane k-1, plane k,
+    // plane k+1) in rotation, so no values are moved between steps.
+    T ra[MAXG][VEC], rb[MAXG][VEC], rc[MAXG][VEC];
 #pragma unroll
     for (int q = 0; q < MAXG; ++q)
 #pragma unroll
-        for (int l = 0; l < VEC; ++l) av[q][l] = bv[q][l] = T(0);
+        for (int l = 0; l < VEC; ++l) ra[q][l] = rb[q][l] = rc[q][l] = T(0);
     if (zo0 > zi0) {
         wait(in_full, 0);
 #pragma unroll
         for (int q = 0; q < MAXG; ++q)
-            if (flags[q] & 1u) ldv(ring + goff[q], av[q]);
+            if (flags[q] & 1u) ldv(ring + goff[q], ra[q]);
     }
     {
         const int n = zo0 - zi0;
@@ -365,25 +378,26 @@ __global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_
         const T *pl = ring + (n & rmask) * slot_elems;
 #pragma unroll
         for (int q = 0; q < MAXG; ++q)
-            if (flags[q] & 1u) ldv(pl + goff[q], bv[q]);
+            if (flags[q] & 1u) ldv(pl + goff[q], rb[q]);
     }
 
-    for (int k = zo0; k < zo1; ++k) {
+    // One output plane k: A = values at k-1, B = at k (own cells), C is
+    // loaded with k+1.  FAST: every cell of this level's region is an
+    // interior cell of the grid and k is an interior plane, so no lane keeps
+    // its own value (lanes of edge groups outside the region compute values
+    // nobody reads).
+    auto step = [&](const int k, T(&A)[MAXG][VEC], T(&B)[MAXG][VEC], T(&C)[MAXG][VEC], auto fast_tag) {
+        constexpr bool FAST = decltype(fast_tag)::value;
         const int n = k - zi0, m = k - zo0;
         issue_upto(n + L);
-        const bool has_next = (k + 1 < zi1);
-        const bool interior_k = (k >= 1 && k <= nz);
-        T cv[MAXG][VEC];
-#pragma unroll
-        for (int q = 0; q < MAXG; ++q)
-#pragma unroll
-            for (int l = 0; l < VEC; ++l) cv[q][l] = T(0);
+        const bool has_next = FAST || (k + 1 < zi1);
+        const bool interior_k = FAST || (k >= 1 && k <= nz);
         if (has_next) {
             wait(in_full + 8u * ((n + 1) & rmask), ((n + 1) >> rsh) & 1);
             const T *pl = ring + ((n + 1) & rmask) * slot_elems;
 #pragma unroll
             for (int q = 0; q < MAXG; ++q)
-                if (flags[q] & 1u) ldv(pl + goff[q], cv[q]);
+                if (flags[q] & 1u) ldv(pl + goff[q], C[q]);
         }
         if (lvl < D && m >= R) wait(out_empty + 8u * (m & rmask), ((m >> rsh) - 1) & 1);
 
@@ -396,9 +410,7 @@ __global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_
             const uint32_t f = flags[q];
             if (!(f & 1u)) continue;
             T v[VEC];
-#pragma unroll
-            for (int l = 0; l < VEC; ++l) v[l] = bv[q][l];
-            if (interior_k && (f & 2u)) {
+            if (FAST || (interior_k && (f & 2u))) {
                 const T *c = cen + goff[q];
                 T sv[VEC], nv[VEC];
                 ldv(c - Wp, sv);
@@ -406,11 +418,14 @@ __global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_
                 const T wv = c[-1], ev = c[VEC];
 #pragma unroll
                 for (int l = 0; l < VEC; ++l) {
-                    const T left = (l == 0) ? wv : bv[q][l - 1];
-                    const T right = (l == VEC - 1) ? ev : bv[q][l + 1];
-                    const T u = Arith<T>::update(left, right, sv[l], nv[l], av[q][l], cv[q][l]);
-                    if (f & (4u << l)) v[l] = u;
+                    const T left = (l == 0) ? wv : B[q][l - 1];
+                    const T right = (l == VEC - 1) ? ev : B[q][l + 1];
+                    const T u = Arith<T>::update(left, right, sv[l], nv[l], A[q][l], C[q][l]);
+                    v[l] = (FAST || (f & (4u << l))) ? u : B[q][l];
                 }
+            } else {
+#pragma unroll
+                for (int l = 0; l < VEC; ++l) v[l] = B[q][l];
             }
             if (lvl < D) {
                 st_async_v(out_base + (uint32_t)goff[q] * (uint32_t)sizeof(T), v, out_bar);
@@ -431,15 +446,45 @@ __global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_
                         if (f & (256u << l)) gpo[l] = v[l];
                 }
             }
-#pragma unroll
-            for (int l = 0; l < VEC; ++l) {
-                av[q][l] = bv[q][l];
-                bv[q][l] = cv[q][l];
-            }
         }
         if (k == zo0 && zo0 > zi0) release(n - 1);
         release(n);
+    };
+    using Fast = std::integral_constant<bool, true>;
+    using Slow = std::integral_constant<bool, false>;
+
+    // Tiles whose widest region (level 1) avoids the grid's x/y halo take
+    // the fast step on their interior planes; halo planes (k = 0, nz+1)
+    // and boundary tiles take the general step.
+    const bool fast_tile = (x0 - (D - 1) >= 1) && (x1 + (D - 1) <= nx + 1) && (y0 - (D - 1) >= 1) &&
+                           (y1 + (D - 1) <= ny + 1);
+    const int kf0 = fast_tile ? max(zo0, 1) : zo1;  // fast steps cover [kf0, kf1)
+    const int kf1 = fast_tile ? min(zo1, nz + 1) : zo1;
+    int k = zo0, rot = 0;  // rot: which register set holds plane k-1
+    auto run = [&](int kk, auto tag) {
+        if (rot == 0) step(kk, ra, rb, rc, tag);
+        else if (rot == 1) step(kk, rb, rc, ra, tag);
+        else step(kk, rc, ra, rb, tag);
+        rot = (rot == 2) ? 0 : rot + 1;
+    };
+    for (; k < kf0; ++k) run(k, Slow());
+    for (; k + 2 < kf1; k += 3) {  // three steps bring the roles back to rot
+        if (rot == 0) {
+            step(k, ra, rb, rc, Fast());
+            step(k + 1, rb, rc, ra, Fast());
+            step(k + 2, rc, ra, rb, Fast());
+        } else if (rot == 1) {
+            step(k, rb, rc, ra, Fast());
+            step(k + 1, rc, ra, rb, Fast());
+            step(k + 2, ra, rb, rc, Fast());
+        } else {
+            step(k, rc, ra, rb, Fast());
+            step(k + 1, ra, rb, rc, Fast());
+            step(k + 2, rb, rc, ra, Fast());
+        }
     }
+    for (; k < kf1; ++k) run(k, Fast());
+    for (; k < zo1; ++k) run(k, Slow());
     cp_async_wait_all();
     cluster_sync_all();
 }

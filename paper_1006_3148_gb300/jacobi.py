@@ -83,6 +83,8 @@ def load(build_if_missing: bool = True):
             "jacobi_batch_get_info": ([P, pi, pi, pi, ctypes.POINTER(ctypes.c_longlong), pi], i),
             "jacobi_batch_get_status": ([P, pi], i),
             "jacobi_batch_debug_set_fault": ([P, i, i], i),
+            "jacobi_check_addition": ([ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong),
+                                       ctypes.POINTER(ctypes.c_ulonglong)], i),
             "jacobi_check_division": ([ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong),
                                        ctypes.POINTER(ctypes.c_ulonglong)], i),
             "jacobi_profile_read": ([P, ctypes.POINTER(d), pi, pi], i),
@@ -375,3 +377,11 @@ def jacobi_poisson_residual_noalloc(u: torch.Tensor, f: torch.Tensor, hgrid: flo
                                                   _stream(stream), ctypes.byref(rel)),
            "jacobi_poisson_residual_noalloc")
     return rel.value
+
+
+def jacobi_check_addition(count: int, seed: int = 1) -> tuple:
+    """(mismatches, failing pair) of the integer-pipe FP64 addition."""
+    m = ctypes.c_ulonglong()
+    f = (ctypes.c_ulonglong * 2)()
+    _check(load().jacobi_check_addition(int(count), int(seed), ctypes.byref(m), f), "jacobi_check_addition")
+    return m.value, (f[0], f[1])

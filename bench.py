@@ -126,6 +126,23 @@ def _dist():
     return dist, rank, ws, local
 
 
+def reduce_max(dist, x: float, device) -> float:
+    """Max of a per-rank float over all ranks (identity without a process
+    group); `device` is where the collective's tensor lives (the GPU for
+    NCCL, the CPU for gloo)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_glups(ws: int, lups_per_step: float, steps: int, max_ms: float) -> float:
+    """Whole-job GLUP/s: every rank sweeps its own replica (weak scaling)."""
+    return ws * lups_per_step * steps / (max_ms * 1e-3) / 1e9
+
+
 def _make_grid(w, device):
     import torch
     from paper_1006_3148_gb300 import inputs
@@ -254,11 +271,8 @@ def run_ours(args, w):
     ms = e0.elapsed_time(e1)
     prof = J.jacobi_profile_read(h)
     assert J.jacobi_get_status(h) == 0, "device status word set during the timed region"
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * lups_step * args.steps / (ms * 1e-3) / 1e9
+    ms = reduce_max(dist, ms, dev)
+    value = aggregate_glups(ws, lups_step, args.steps, ms)
 
     # ---- roofline of the dominant kernel (the pass kernel), live events
     peaks, peak_src = _peaks()
@@ -337,10 +351,7 @@ def run_ours(args, w):
         for _ in range(ke):
             J.jacobi_sweep_host(h, host_in, host_out, T, stream)
         dt_e = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt_e], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt_e = float(t.item())
+        dt_e = reduce_max(dist, dt_e, dev)
         nbytes = host_in.numel() * es
         line["e2e"] = {"value": ws * lups_step * ke / dt_e / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes, "steps": ke}
@@ -414,10 +425,7 @@ def run_batch(args, w):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     assert J.jacobi_batch_get_status(b) == 0
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(dist, ms, dev)
     step_s = ms * 1e-3 / args.steps
     value = ws * lups / step_s / 1e9
     peaks, peak_src = _peaks()

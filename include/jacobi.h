@@ -104,29 +104,35 @@ int jacobi_sweep(jacobi_h h, void *A, void *B, int T, jacobi_stream_t stream);
 int jacobi_sweep_host(jacobi_h h, const void *A_host, void *out_host, int T,
                       jacobi_stream_t stream);
 
-/* Forces a plan: kernel (JACOBI_KERNEL_*), temporal depth (1..16; 1 for
- * PLAIN), tile interior bx*by (bx, by >= 1), z chunk bz >= 1 interior
- * planes per cluster, ring = plane slots between two pipeline levels
- * (4, 8 or 16; 0 = the deepest that fits 100 KB of shared memory), and
- * threads = CTA width (128, 256 or 512; 0 = automatic).  The
+/* Forces a plan: kernel (JACOBI_KERNEL_*) and temporal depth (1..16;
+ * taken as 1 for PLAIN).  For TB: tile interior bx*by (bx, by >= 1), z chunk
+ * bz >= 1 interior planes per cluster, ring = plane slots between two
+ * pipeline levels (4, 8 or 16; 0 = the deepest that fits 100 KB of shared
+ * memory), and threads = CTA width (128, 256 or 512; 0 = automatic).  The
  * ring depth is the pipeline looseness of Sect. 2.2 (a producer may run up
  * to ring planes ahead of its consumer; at least one plane, Eq. 3).
- * bz, ring and threads are ignored by PLAIN.  Depths > 8 need the non-portable
- * cluster size.  JACOBI_KERNEL_AUTO returns to the tuned/default plan.
- * Returns JACOBI_ERR_UNSUPPORTED if the plan cannot launch on this device
- * (shared memory, registers, cluster occupancy). */
+ * Depths > 8 need the non-portable cluster size.  For PLAIN: bx*by = CTA
+ * shape in cells (bx a multiple of 32, bx*by <= 1024) and bz = planes each
+ * thread walks in z; ring and threads are ignored.  A zero bx, by or bz
+ * takes the family's default (PLAIN 32 x 8 x 8; TB 64 x 16 x 64, clamped to
+ * the grid).  JACOBI_KERNEL_AUTO returns to the tuned/default plan.
+ * Returns JACOBI_ERR_ARG for out-of-range fields and JACOBI_ERR_UNSUPPORTED
+ * if the plan cannot launch on this device (shared memory, registers,
+ * cluster occupancy). */
 int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, int ring,
                     int threads);
 
-/* Reads back the plan jacobi_sweep will use (ring/threads 0 = automatic). */
+/* Reads back the plan jacobi_sweep will use, defaults resolved
+ * (ring/threads 0 = automatic). */
 int jacobi_get_plan(jacobi_h h, int *kernel, int *depth, int *bx, int *by, int *bz, int *ring,
                     int *threads);
 
 /* Autotuner (experiment-driven parameter choice, Sect. 2.4): fills the
  * caller's scratch grids (same size as the handle's grids; contents
  * overwritten, never the user's data) with a constant and times candidate
- * plans on them -- the single-pass kernel, and pass kernels of depth 1..8
- * over tile shapes, then z chunks and ring depths around the best -- and
+ * plans on them -- the single-pass kernel over CTA shapes and planes per
+ * thread, and pass kernels of depth 1..8 over tile shapes, then z chunks,
+ * ring depths and CTA widths around the best -- and
  * keeps the fastest as the handle's AUTO plan.  Results are
  * cached per process by (dtype, nx, ny, nz, SM count).  Synchronises
  * stream.  *glups (may be NULL) receives the best measured GLUP/s. */

@@ -3,6 +3,7 @@
 // host or library fallback for any part of a sweep.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -82,9 +83,26 @@ bool prof_event(jacobi_plan_s *h, cudaStream_t s)
     return cudaEventRecord(h->ev_pool[h->ev_used++], s) == cudaSuccess;
 }
 
+// Replaces zero tile fields of a forced plan by the kernel family's defaults
+// (PLAIN: 32 x 8 threads, 8 planes per thread; TB: 64 x 16 tile, 64 planes).
+Plan resolve_plan(const jacobi_plan_s *h, Plan p)
+{
+    const bool plain = p.kernel == JACOBI_KERNEL_PLAIN;
+    if (p.bx == 0) p.bx = plain ? 32 : std::min(64, h->nx);
+    if (p.by == 0) p.by = plain ? 8 : std::min(16, h->ny);
+    if (p.bz == 0) p.bz = plain ? 8 : std::min(64, h->nz);
+    return p;
+}
+
 int check_plan(const jacobi_plan_s *h, const Plan &p)
 {
-    if (p.kernel == JACOBI_KERNEL_PLAIN) return JACOBI_OK;
+    if (p.kernel == JACOBI_KERNEL_PLAIN) {
+        if (p.bx < 32 || p.bx % 32 != 0 || p.by < 1 || (long long)p.bx * p.by > 1024 || p.bz < 1)
+            return JACOBI_ERR_ARG;
+        // (row block, z chunk) pairs must fit grid y * grid z
+        const long long pairs = (long long)((h->ny + p.by - 1) / p.by) * ((h->nz + p.bz - 1) / p.bz);
+        return pairs <= 65535ll * 65535ll ? JACOBI_OK : JACOBI_ERR_UNSUPPORTED;
+    }
     if (p.kernel != JACOBI_KERNEL_TB) return JACOBI_ERR_ARG;
     if (p.depth < 1 || p.depth > 16 || p.bx < 1 || p.by < 1 || p.bz < 1) return JACOBI_ERR_ARG;
     if (p.ring != 0 && p.ring != 4 && p.ring != 8 && p.ring != 16) return JACOBI_ERR_ARG;
@@ -112,7 +130,9 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
         a.nx = h->nx;
         a.ny = h->ny;
         a.nz = h->nz;
-        a.kz = 8;
+        a.kz = p.bz;
+        a.tx = p.bx;
+        a.ty = p.by;
         for (int t = 0; t < T; ++t) {
             a.src = (t % 2 == 0) ? A : B;
             a.dst = (t % 2 == 0) ? B : A;
@@ -284,6 +304,7 @@ int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, i
         h->forced = false;
         return JACOBI_OK;
     }
+    if (bx < 0 || by < 0 || bz < 0) return JACOBI_ERR_ARG;
     Plan p;
     p.kernel = kernel;
     p.depth = (kernel == JACOBI_KERNEL_PLAIN) ? 1 : depth;
@@ -292,6 +313,7 @@ int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, i
     p.bz = bz;
     p.ring = (kernel == JACOBI_KERNEL_PLAIN) ? 0 : ring;
     p.threads = (kernel == JACOBI_KERNEL_PLAIN) ? 0 : threads;
+    p = resolve_plan(h, p);
     const int st = check_plan(h, p);
     if (st != JACOBI_OK) return st;
     h->plan = p;
@@ -452,13 +474,19 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
     };
     const int *dl = f64 ? depths64 : depths32;
     const int nd = f64 ? 3 : 5;
-    {
-        Plan p;  // the single-pass kernel competes too
-        p.kernel = JACOBI_KERNEL_PLAIN;
-        p.depth = 1;
-        p.bx = p.by = p.bz = 1;
-        consider(p);
-    }
+    // The single-pass kernel competes too: CTA shapes x planes per thread.
+    const int plain_shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {32, 16}, {64, 8}, {128, 4}, {256, 2}, {64, 16}};
+    const int plain_kz[] = {4, 8, 16, 32};
+    for (const auto &b : plain_shapes)
+        for (int kz : plain_kz) {
+            Plan p;
+            p.kernel = JACOBI_KERNEL_PLAIN;
+            p.depth = 1;
+            p.bx = b[0];
+            p.by = b[1];
+            p.bz = kz;
+            consider(p);
+        }
     for (int di = 0; di < nd; ++di)
         for (const auto &t : tiles) {
             Plan p;

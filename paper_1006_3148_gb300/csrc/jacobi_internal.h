@@ -30,10 +30,14 @@ struct PlainArgs {
     const void *src;
     void *dst;
     int nx, ny, nz;
-    int kz;  // planes per thread
+    int kz;      // planes per thread
+    int tx, ty;  // CTA shape in cells
+    int gy, gz;  // row blocks, z chunks (set by plain_launch)
 };
 
 // Plan of one handle.
+// PLAIN: bx x by = CTA shape in cells, bz = planes per thread.
+// TB: bx x by = tile interior, bz = interior planes per cluster.
 struct Plan {
     int kernel = JACOBI_KERNEL_TB;
     int depth = 1;
@@ -55,7 +59,7 @@ struct TbLaunch {
 cudaError_t tb_configure(int dtype, int depth, int bx, int by, int ring, int threads, TbLaunch *out);
 cudaError_t tb_launch(int dtype, const TbArgs &a, const TbLaunch &L, cudaStream_t s);
 cudaError_t tb_max_clusters(int dtype, const TbLaunch &L, int depth, int *clusters);
-cudaError_t plain_launch(int dtype, const PlainArgs &a, cudaStream_t s);
+cudaError_t plain_launch(int dtype, PlainArgs a, cudaStream_t s);
 cudaError_t fill_launch(int dtype, void *p, long long n, double v, cudaStream_t s);
 cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, int nz, cudaStream_t s);
 

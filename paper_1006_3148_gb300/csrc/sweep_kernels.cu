@@ -85,14 +85,21 @@ __global__ void fill_kernel(T *p, long long n, T v)
 // values at k-1, k, k+1 in registers; the four in-plane neighbours come from
 // global memory (mostly L1 hits: neighbouring threads load them too).
 template <typename T>
-__global__ void __launch_bounds__(256) plain_pass_kernel(const PlainArgs a)
+__global__ void __launch_bounds__(1024) plain_pass_kernel(const PlainArgs a)
 {
+    // (row block, z chunk) pairs are numbered t = yb + gy * zc and spread
+    // over grid y and z (each at most 65535 blocks).  A loop over several
+    // pairs per block would be simpler but costs a third of the bandwidth
+    // (the compiler then schedules the plane loop's loads less well).
+    const long long t = blockIdx.y + (long long)gridDim.y * blockIdx.z;
+    if (t >= (long long)a.gy * a.gz) return;
+    const int yb = (int)(t % a.gy), zc = (int)(t / a.gy);
     const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    const int j = 1 + yb * blockDim.y + threadIdx.y;
     if (i > a.nx || j > a.ny) return;
     const long long NXP = a.nx + 2, plane = NXP * (a.ny + 2);
-    const int kb = 1 + blockIdx.z * a.kz;
-    const int ke = min(kb + a.kz, a.nz + 1);
+    const int kb = 1 + zc * a.kz;
+    const int ke = (a.nz + 1 - kb < a.kz) ? a.nz + 1 : kb + a.kz;
     const long long c0 = kb * plane + j * NXP + i;
     const T *__restrict__ p = static_cast<const T *>(a.src) + c0;
     T *__restrict__ q = static_cast<T *>(a.dst) + c0;
@@ -638,10 +645,15 @@ cudaError_t tb_max_clusters(int dtype, const TbLaunch &L, int depth, int *cluste
     return cudaOccupancyMaxActiveClusters(clusters, fn, &cfg);
 }
 
-cudaError_t plain_launch(int dtype, const PlainArgs &a, cudaStream_t s)
+cudaError_t plain_launch(int dtype, PlainArgs a, cudaStream_t s)
 {
-    dim3 block(32, 8, 1);
-    dim3 grid((unsigned)((a.nx + 31) / 32), (unsigned)((a.ny + 7) / 8), (unsigned)((a.nz + a.kz - 1) / a.kz));
+    a.gy = (a.ny + a.ty - 1) / a.ty;
+    a.gz = (a.nz + a.kz - 1) / a.kz;
+    const long long pairs = (long long)a.gy * a.gz;
+    const long long by = std::min<long long>(pairs, 65535), bz = (pairs + by - 1) / by;
+    if (bz > 65535) return cudaErrorInvalidConfiguration;
+    dim3 block((unsigned)a.tx, (unsigned)a.ty, 1);
+    dim3 grid((unsigned)((a.nx + a.tx - 1) / a.tx), (unsigned)by, (unsigned)bz);
     if (dtype == JACOBI_F64) plain_pass_kernel<double><<<grid, block, 0, s>>>(a);
     else plain_pass_kernel<float><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();

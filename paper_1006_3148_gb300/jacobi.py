@@ -183,7 +183,7 @@ def jacobi_sweep_host(h: Handle, A_host: torch.Tensor, out_host: torch.Tensor, T
     return out_host
 
 
-def jacobi_set_plan(h: Handle, kernel: int, depth: int = 1, bx: int = 64, by: int = 16, bz: int = 64,
+def jacobi_set_plan(h: Handle, kernel: int, depth: int = 1, bx: int = 0, by: int = 0, bz: int = 0,
                     ring: int = 0, threads: int = 0):
     _check(load().jacobi_set_plan(h.ptr, int(kernel), int(depth), int(bx), int(by), int(bz), int(ring),
                                   int(threads)), "jacobi_set_plan")

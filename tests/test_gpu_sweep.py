@@ -46,7 +46,7 @@ def _gpu(shape, seed, dtype, T, plan=None, A0=None):
 
 SHAPES = [(1, 1, 1), (2, 3, 1), (5, 4, 3), (7, 9, 11), (13, 6, 17), (33, 31, 29), (67, 45, 33)]
 PLANS = [
-    (J.KERNEL_PLAIN, 1, 1, 1, 1),
+    (J.KERNEL_PLAIN, 1, 32, 8, 8),
     (J.KERNEL_TB, 1, 4, 3, 2),
     (J.KERNEL_TB, 1, 8, 8, 8),
     (J.KERNEL_TB, 1, 64, 16, 64),
@@ -61,6 +61,9 @@ PLANS = [
     (J.KERNEL_TB, 1, 32, 8, 16, 8),
     (J.KERNEL_TB, 2, 16, 8, 8, 4, 128),
     (J.KERNEL_TB, 3, 24, 12, 8, 8, 512),
+    (J.KERNEL_PLAIN, 1, 64, 4, 1),
+    (J.KERNEL_PLAIN, 1, 128, 8, 3),
+    (J.KERNEL_PLAIN, 1, 32, 32, 32),
 ]
 
 
@@ -89,7 +92,7 @@ def test_workload_64cubed_fp64_all_depths():
     # 64^3 interior, interior and halo U[0,1) from seed 1, T = 10
     shape = (64, 64, 64)
     exp = _expected(shape, 1, torch.float64, 10)
-    for plan in [None, (J.KERNEL_PLAIN, 1, 1, 1, 1)] + [(J.KERNEL_TB, d, 32, 16, 32) for d in (1, 2, 4, 8)]:
+    for plan in [None, (J.KERNEL_PLAIN, 1, 0, 0, 0)] + [(J.KERNEL_TB, d, 32, 16, 32) for d in (1, 2, 4, 8)]:
         got = _gpu(shape, 1, torch.float64, 10, plan)
         assert np.array_equal(got, exp), plan
 
@@ -126,6 +129,27 @@ def test_argument_errors():
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 1, 8, 8, 8, 5, 0) == -1
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 1, 8, 8, 8, 4, 96) == -1
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 8, 512, 512, 8, 0, 0) == -9
+    # PLAIN: CTA x extent a multiple of 32, at most 1024 threads, planes >= 0
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_PLAIN, 1, 48, 4, 8, 0, 0) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_PLAIN, 1, 64, 32, 8, 0, 0) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_PLAIN, 1, 32, 8, -1, 0, 0) == -1
+    J.jacobi_set_plan(h, J.KERNEL_PLAIN)
+    p = J.jacobi_get_plan(h)
+    assert (p["kernel"], p["depth"], p["bx"], p["by"], p["bz"]) == (J.KERNEL_PLAIN, 1, 32, 8, 8)
+    J.jacobi_set_plan(h, J.KERNEL_TB, 2)
+    p = J.jacobi_get_plan(h)
+    assert (p["kernel"], p["depth"], p["bx"], p["by"], p["bz"]) == (J.KERNEL_TB, 2, 8, 8, 8)
+
+
+@pytest.mark.parametrize("shape,plan", [((1, 70000, 2), (J.KERNEL_PLAIN, 1, 32, 1, 1)),
+                                        ((3, 1, 70001), (J.KERNEL_PLAIN, 1, 32, 1, 1)),
+                                        ((40, 3, 65600), (J.KERNEL_PLAIN, 1, 32, 1, 1))])
+def test_plain_grid_stride_beyond_65535_blocks(shape, plan):
+    # grid y / z are capped at 65535 blocks; the remaining rows and z chunks
+    # are covered by the kernel's grid-stride loops
+    for T in (1, 2):
+        got = _gpu(shape, 13, torch.float64, T, plan)
+        assert np.array_equal(got, _expected(shape, 13, torch.float64, T)), (shape, T)
 
 
 def test_bounded_wait_timeout_reports_status_and_context_survives():

@@ -236,7 +236,7 @@ def run_ours(args, w):
         f = args.plan.split(":")
         ring = int(f[5]) if len(f) > 5 else 0
         threads = int(f[6]) if len(f) > 6 else 0
-        J.jacobi_set_plan(h, {"tb": J.KERNEL_TB, "plain": J.KERNEL_PLAIN}[f[0]], int(f[1]), int(f[2]), int(f[3]),
+        J.jacobi_set_plan(h, {"tb": J.KERNEL_TB, "plain": J.KERNEL_PLAIN, "x2": J.KERNEL_PLAIN_X2}[f[0]], int(f[1]), int(f[2]), int(f[3]),
                           int(f[4]), ring, threads)
     elif not args.no_tune:
         sa, sb = torch.empty_like(A), torch.empty_like(A)
@@ -300,7 +300,8 @@ def run_ours(args, w):
     if roof is None:
         roof = {"bound": "hbm", "achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
                 "traffic": None, "peak_source": peak_src}
-    roof["kernel"] = "tb_pass_kernel" if plan["kernel"] == J.KERNEL_TB else "plain_pass_kernel"
+    roof["kernel"] = {J.KERNEL_TB: "tb_pass_kernel", J.KERNEL_PLAIN: "plain_pass_kernel",
+                      J.KERNEL_PLAIN_X2: "plain_x2_kernel"}[plan["kernel"]]
     roof["avg_launch_ms"] = pass_ms
     roof["sm_mhz_during"] = clk
 

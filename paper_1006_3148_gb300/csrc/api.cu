@@ -84,19 +84,22 @@ bool prof_event(jacobi_plan_s *h, cudaStream_t s)
 }
 
 // Replaces zero tile fields of a forced plan by the kernel family's defaults
-// (PLAIN: 32 x 8 threads, 8 planes per thread; TB: 64 x 16 tile, 64 planes).
+// (PLAIN: 32 x 8 threads, 8 planes per thread; PLAIN_X2: 32 x 8 threads,
+// 16 planes; TB: 64 x 16 tile, 64 planes).
 Plan resolve_plan(const jacobi_plan_s *h, Plan p)
 {
-    const bool plain = p.kernel == JACOBI_KERNEL_PLAIN;
+    const bool plain = p.kernel == JACOBI_KERNEL_PLAIN || p.kernel == JACOBI_KERNEL_PLAIN_X2;
     if (p.bx == 0) p.bx = plain ? 32 : std::min(64, h->nx);
     if (p.by == 0) p.by = plain ? 8 : std::min(16, h->ny);
-    if (p.bz == 0) p.bz = plain ? 8 : std::min(64, h->nz);
+    if (p.bz == 0) p.bz = plain ? (p.kernel == JACOBI_KERNEL_PLAIN_X2 ? 16 : 8) : std::min(64, h->nz);
     return p;
 }
 
 int check_plan(const jacobi_plan_s *h, const Plan &p)
 {
-    if (p.kernel == JACOBI_KERNEL_PLAIN) {
+    if (p.kernel == JACOBI_KERNEL_PLAIN_X2 && (h->dtype != JACOBI_F32 || h->nx % 2 != 0))
+        return JACOBI_ERR_UNSUPPORTED;
+    if (p.kernel == JACOBI_KERNEL_PLAIN || p.kernel == JACOBI_KERNEL_PLAIN_X2) {
         if (p.bx < 32 || p.bx % 32 != 0 || p.by < 1 || (long long)p.bx * p.by > 1024 || p.bz < 1)
             return JACOBI_ERR_ARG;
         // (row block, z chunk) pairs must fit grid y * grid z
@@ -125,7 +128,7 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
     cudaError_t e = halo_copy_launch(h->dtype, A, B, h->nx, h->ny, h->nz, s);
     if (e != cudaSuccess) return cuda_fail(e);
     if (h->prof) ++h->prof_other;
-    if (p.kernel == JACOBI_KERNEL_PLAIN) {
+    if (p.kernel == JACOBI_KERNEL_PLAIN || p.kernel == JACOBI_KERNEL_PLAIN_X2) {
         PlainArgs a;
         a.nx = h->nx;
         a.ny = h->ny;
@@ -137,7 +140,7 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
             a.src = (t % 2 == 0) ? A : B;
             a.dst = (t % 2 == 0) ? B : A;
             if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
-            e = plain_launch(h->dtype, a, s);
+            e = (p.kernel == JACOBI_KERNEL_PLAIN_X2) ? plain_x2_launch(a, s) : plain_launch(h->dtype, a, s);
             if (e != cudaSuccess) return cuda_fail(e);
             if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
             if (h->prof) ++h->prof_pass;
@@ -307,12 +310,13 @@ int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, i
     if (bx < 0 || by < 0 || bz < 0) return JACOBI_ERR_ARG;
     Plan p;
     p.kernel = kernel;
-    p.depth = (kernel == JACOBI_KERNEL_PLAIN) ? 1 : depth;
+    const bool plain = kernel == JACOBI_KERNEL_PLAIN || kernel == JACOBI_KERNEL_PLAIN_X2;
+    p.depth = plain ? 1 : depth;
     p.bx = bx;
     p.by = by;
     p.bz = bz;
-    p.ring = (kernel == JACOBI_KERNEL_PLAIN) ? 0 : ring;
-    p.threads = (kernel == JACOBI_KERNEL_PLAIN) ? 0 : threads;
+    p.ring = plain ? 0 : ring;
+    p.threads = plain ? 0 : threads;
     p = resolve_plan(h, p);
     const int st = check_plan(h, p);
     if (st != JACOBI_OK) return st;
@@ -477,16 +481,17 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
     // The single-pass kernel competes too: CTA shapes x planes per thread.
     const int plain_shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {32, 16}, {64, 8}, {128, 4}, {256, 2}, {64, 16}};
     const int plain_kz[] = {4, 8, 16, 32};
-    for (const auto &b : plain_shapes)
-        for (int kz : plain_kz) {
-            Plan p;
-            p.kernel = JACOBI_KERNEL_PLAIN;
-            p.depth = 1;
-            p.bx = b[0];
-            p.by = b[1];
-            p.bz = kz;
-            consider(p);
-        }
+    for (int kern : {JACOBI_KERNEL_PLAIN, JACOBI_KERNEL_PLAIN_X2})
+        for (const auto &b : plain_shapes)
+            for (int kz : plain_kz) {
+                Plan p;
+                p.kernel = kern;
+                p.depth = 1;
+                p.bx = b[0];
+                p.by = b[1];
+                p.bz = kz;
+                consider(p);
+            }
     for (int di = 0; di < nd; ++di)
         for (const auto &t : tiles) {
             Plan p;

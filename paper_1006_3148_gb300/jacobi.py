@@ -17,7 +17,7 @@ from . import build as _build
 
 F64 = 0
 F32 = 1
-KERNEL_AUTO, KERNEL_PLAIN, KERNEL_TB = 0, 1, 2
+KERNEL_AUTO, KERNEL_PLAIN, KERNEL_TB, KERNEL_PLAIN_X2 = 0, 1, 2, 3
 
 STATUS = {
     0: "JACOBI_OK", -1: "JACOBI_ERR_ARG", -2: "JACOBI_ERR_DTYPE", -3: "JACOBI_ERR_ALLOC",

@@ -562,7 +562,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fp64_512", choices=sorted(WORKLOADS))
-    ap.add_argument("--plan", default=None, help="force a plan kernel:depth:bx:by:bz[:ring], e.g. tb:4:64:16:64:8 or plain:1:1:1:1")
+    ap.add_argument("--plan", default=None, help="force a plan kernel:depth:bx:by:bz[:ring[:threads]], kernel tb, plain or x2, e.g. tb:4:64:16:64:8 or x2:1:32:8:16")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

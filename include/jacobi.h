@@ -64,8 +64,8 @@ enum {
     JACOBI_KERNEL_TB = 2,    /* z-streaming pass; depth d > 1 runs the
                                 time-skewed cluster pipeline                  */
     JACOBI_KERNEL_PLAIN_X2 = 3 /* single-pass kernel with two x cells per
-                                thread (packed FP32 arithmetic); FP32 grids
-                                with even nx only                             */
+                                thread (vector loads, shuffled x-neighbours,
+                                packed FP32 additions); even nx only          */
 };
 
 typedef struct jacobi_plan_s *jacobi_h;

@@ -97,7 +97,7 @@ Plan resolve_plan(const jacobi_plan_s *h, Plan p)
 
 int check_plan(const jacobi_plan_s *h, const Plan &p)
 {
-    if (p.kernel == JACOBI_KERNEL_PLAIN_X2 && (h->dtype != JACOBI_F32 || h->nx % 2 != 0))
+    if (p.kernel == JACOBI_KERNEL_PLAIN_X2 && h->nx % 2 != 0)
         return JACOBI_ERR_UNSUPPORTED;
     if (p.kernel == JACOBI_KERNEL_PLAIN || p.kernel == JACOBI_KERNEL_PLAIN_X2) {
         if (p.bx < 32 || p.bx % 32 != 0 || p.by < 1 || (long long)p.bx * p.by > 1024 || p.bz < 1)
@@ -140,7 +140,7 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
             a.src = (t % 2 == 0) ? A : B;
             a.dst = (t % 2 == 0) ? B : A;
             if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
-            e = (p.kernel == JACOBI_KERNEL_PLAIN_X2) ? plain_x2_launch(a, s) : plain_launch(h->dtype, a, s);
+            e = (p.kernel == JACOBI_KERNEL_PLAIN_X2) ? plain_x2_launch(h->dtype, a, s) : plain_launch(h->dtype, a, s);
             if (e != cudaSuccess) return cuda_fail(e);
             if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
             if (h->prof) ++h->prof_pass;

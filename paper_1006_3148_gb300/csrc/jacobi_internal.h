@@ -60,7 +60,7 @@ cudaError_t tb_configure(int dtype, int depth, int bx, int by, int ring, int thr
 cudaError_t tb_launch(int dtype, const TbArgs &a, const TbLaunch &L, cudaStream_t s);
 cudaError_t tb_max_clusters(int dtype, const TbLaunch &L, int depth, int *clusters);
 cudaError_t plain_launch(int dtype, PlainArgs a, cudaStream_t s);
-cudaError_t plain_x2_launch(PlainArgs a, cudaStream_t s);  // FP32, nx even
+cudaError_t plain_x2_launch(int dtype, PlainArgs a, cudaStream_t s);  // nx even
 cudaError_t fill_launch(int dtype, void *p, long long n, double v, cudaStream_t s);
 cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, int nz, cudaStream_t s);
 

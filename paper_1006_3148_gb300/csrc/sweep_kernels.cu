@@ -116,17 +116,47 @@ __global__ void __launch_bounds__(1024) plain_pass_kernel(const PlainArgs a)
     }
 }
 
-// FP32 single-pass kernel with two x cells per thread (rows of even pitch,
-// nx even).  Thread pair m of a row covers cells (2m, 2m+1), so the pairs
-// tile the whole row, halo cells included; every value is one aligned
-// 8-byte load.  The x-neighbours come from the adjacent lanes' centre values
-// (shuffles; lanes 0 and 31 load the cell beyond their pair), the y- and
-// z-neighbours are float2 loads, and both cells' Eq. (1) sums run as packed
-// FP32 additions in the same left-to-right order as the scalar kernel.
-// Halo cells (x = 0, nx+1) are written back with their own value, which
-// equals the destination's halo.
+// Single-pass kernel with two x cells per thread (rows of even pitch, nx
+// even).  Thread pair m of a row covers cells (2m, 2m+1), so the pairs tile
+// the whole row, halo cells included; every value is one aligned 8-byte
+// (FP32) or 16-byte (FP64) load.  The x-neighbours come from the adjacent
+// lanes' centre values (shuffles; lanes 0 and 31 load the cell beyond their
+// pair) and the y- and z-neighbours are vector loads, so a cell costs 1.5
+// vector loads instead of the scalar kernel's five loads.  Both cells' Eq.
+// (1) sums keep the scalar kernel's left-to-right order (FP32: packed
+// additions).  Halo cells (x = 0, nx+1) are written back with their own
+// value, which equals the destination's halo.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using V = float2;
+    static __device__ __forceinline__ V update(float w, V mid, float e, V ym, V yp, V lo, V hi)
+    {
+        V s = __fadd2_rn(make_float2(w, mid.x), make_float2(mid.y, e));
+        s = __fadd2_rn(s, ym);
+        s = __fadd2_rn(s, yp);
+        s = __fadd2_rn(s, lo);
+        s = __fadd2_rn(s, hi);
+        return __fmul2_rn(s, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+    }
+};
+template <>
+struct Pair<double> {
+    using V = double2;
+    static __device__ __forceinline__ V update(double w, V mid, double e, V ym, V yp, V lo, V hi)
+    {
+        V o;
+        o.x = Arith<double>::update(w, mid.y, ym.x, yp.x, lo.x, hi.x);
+        o.y = Arith<double>::update(mid.x, e, ym.y, yp.y, lo.y, hi.y);
+        return o;
+    }
+};
+
+template <typename T>
 __global__ void __launch_bounds__(1024) plain_x2_kernel(const PlainArgs a)
 {
+    using V = typename Pair<T>::V;
     const long long t = blockIdx.y + (long long)gridDim.y * blockIdx.z;
     if (t >= (long long)a.gy * a.gz) return;  // uniform per block
     const int yb = (int)(t % a.gy), zc = (int)(t / a.gy);
@@ -141,19 +171,19 @@ __global__ void __launch_bounds__(1024) plain_x2_kernel(const PlainArgs a)
     const int kb = 1 + zc * a.kz;
     const int ke = (a.nz + 1 - kb < a.kz) ? a.nz + 1 : kb + a.kz;
     const long long c0 = kb * plane + (long long)(live ? j : 1) * NXP + 2 * (long long)(live ? m : 0);
-    const float *__restrict__ p = static_cast<const float *>(a.src) + c0;
-    float *__restrict__ q = static_cast<float *>(a.dst) + c0;
-    const float2 *__restrict__ p2 = reinterpret_cast<const float2 *>(p);
-    float2 *__restrict__ q2 = reinterpret_cast<float2 *>(q);
-    const long long P2 = plane >> 1, R2 = NXP >> 1;  // plane and row in float2
-    const float2 zero = make_float2(0.f, 0.f);
-    const float2 sixth = make_float2(1.0f / 6.0f, 1.0f / 6.0f);
+    const T *__restrict__ p = static_cast<const T *>(a.src) + c0;
+    const V *__restrict__ p2 = reinterpret_cast<const V *>(p);
+    V *__restrict__ q2 = reinterpret_cast<V *>(static_cast<T *>(a.dst) + c0);
+    const long long P2 = plane >> 1, R2 = NXP >> 1;  // plane and row in pairs
+    V zero;
+    zero.x = T(0);
+    zero.y = T(0);
     const bool left_halo = (m == 0), right_halo = (2 * m + 1 == a.nx + 1);
-    float2 lo = live ? __ldg(p2 - P2) : zero, mid = live ? __ldg(p2) : zero;
+    V lo = live ? __ldg(p2 - P2) : zero, mid = live ? __ldg(p2) : zero;
 #pragma unroll 4
     for (int k = kb; k < ke; ++k) {
-        float2 hi = zero, ym = zero, yp = zero;
-        float w = 0.f, e = 0.f;
+        V hi = zero, ym = zero, yp = zero;
+        T w = T(0), e = T(0);
         if (live) {
             hi = __ldg(p2 + P2);
             ym = __ldg(p2 - R2);
@@ -164,16 +194,11 @@ __global__ void __launch_bounds__(1024) plain_x2_kernel(const PlainArgs a)
             if (lane == 0) w = __ldg(p - 1);
             if (lane == 31) e = __ldg(p + 2);
         }
-        const float wl = __shfl_up_sync(0xffffffffu, mid.y, 1);
-        const float er = __shfl_down_sync(0xffffffffu, mid.x, 1);
+        const T wl = __shfl_up_sync(0xffffffffu, mid.y, 1);
+        const T er = __shfl_down_sync(0xffffffffu, mid.x, 1);
         if (lane != 0) w = wl;
         if (lane != 31) e = er;
-        float2 s = __fadd2_rn(make_float2(w, mid.x), make_float2(mid.y, e));
-        s = __fadd2_rn(s, ym);
-        s = __fadd2_rn(s, yp);
-        s = __fadd2_rn(s, lo);
-        s = __fadd2_rn(s, hi);
-        float2 o = __fmul2_rn(s, sixth);
+        V o = Pair<T>::update(w, mid, e, ym, yp, lo, hi);
         if (left_halo) o.x = mid.x;
         if (right_halo) o.y = mid.y;
         if (live) *q2 = o;
@@ -728,7 +753,7 @@ cudaError_t plain_launch(int dtype, PlainArgs a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t plain_x2_launch(PlainArgs a, cudaStream_t s)
+cudaError_t plain_x2_launch(int dtype, PlainArgs a, cudaStream_t s)
 {
     a.gy = (a.ny + a.ty - 1) / a.ty;
     a.gz = (a.nz + a.kz - 1) / a.kz;
@@ -738,7 +763,8 @@ cudaError_t plain_x2_launch(PlainArgs a, cudaStream_t s)
     const int npairs = (a.nx + 2) / 2;
     dim3 block((unsigned)a.tx, (unsigned)a.ty, 1);
     dim3 grid((unsigned)((npairs + a.tx - 1) / a.tx), (unsigned)by, (unsigned)bz);
-    plain_x2_kernel<<<grid, block, 0, s>>>(a);
+    if (dtype == JACOBI_F64) plain_x2_kernel<double><<<grid, block, 0, s>>>(a);
+    else plain_x2_kernel<float><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 

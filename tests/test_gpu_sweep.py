@@ -146,21 +146,22 @@ X2_PLANS = [(J.KERNEL_PLAIN_X2, 1, 32, 1, 1), (J.KERNEL_PLAIN_X2, 1, 32, 8, 16),
             (J.KERNEL_PLAIN_X2, 1, 128, 8, 32)]
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
 @pytest.mark.parametrize("shape", X2_SHAPES)
 @pytest.mark.parametrize("plan", X2_PLANS, ids=lambda p: "x2_%dx%dx%d" % p[2:5])
-def test_fp32_two_cells_per_thread_bitwise(shape, plan):
-    # packed FP32 additions in Eq. (1)'s order give the FP32 oracle's bits
+def test_two_cells_per_thread_bitwise(shape, plan, dtype):
+    # Eq. (1)'s left-to-right order per cell (FP32: packed additions) gives
+    # the oracle's bits
     for T in (1, 4, 9):
-        got = _gpu(shape, 14, torch.float32, T, plan)
-        assert np.array_equal(got, _expected(shape, 14, torch.float32, T)), (shape, plan, T)
+        got = _gpu(shape, 14, dtype, T, plan)
+        assert np.array_equal(got, _expected(shape, 14, dtype, T)), (shape, plan, T)
 
 
-def test_two_cells_per_thread_needs_fp32_and_even_nx():
+def test_two_cells_per_thread_needs_even_nx():
     L = J.load()
-    h64 = J.Handle(8, 8, 8, torch.float64)
-    assert L.jacobi_set_plan(h64.ptr, J.KERNEL_PLAIN_X2, 1, 32, 8, 8, 0, 0) == -9
-    h_odd = J.Handle(9, 8, 8, torch.float32)
-    assert L.jacobi_set_plan(h_odd.ptr, J.KERNEL_PLAIN_X2, 1, 32, 8, 8, 0, 0) == -9
+    for dt in (torch.float64, torch.float32):
+        h_odd = J.Handle(9, 8, 8, dt)
+        assert L.jacobi_set_plan(h_odd.ptr, J.KERNEL_PLAIN_X2, 1, 32, 8, 8, 0, 0) == -9
     h = J.Handle(10, 8, 8, torch.float32)
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_PLAIN_X2, 1, 48, 8, 8, 0, 0) == -1
     J.jacobi_set_plan(h, J.KERNEL_PLAIN_X2)
@@ -173,9 +174,9 @@ def test_two_cells_per_thread_needs_fp32_and_even_nx():
                                         ((40, 3, 65600), (J.KERNEL_PLAIN, 1, 32, 1, 1)),
                                         ((2, 70000, 2), (J.KERNEL_PLAIN_X2, 1, 32, 1, 1)),
                                         ((40, 3, 65600), (J.KERNEL_PLAIN_X2, 1, 32, 1, 1))])
-def test_plain_beyond_65535_row_blocks_or_z_chunks(shape, plan):
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32], ids=["f64", "f32"])
+def test_plain_beyond_65535_row_blocks_or_z_chunks(shape, plan, dt):
     # more (row block, z chunk) pairs than grid y holds: they spill into grid z
-    dt = torch.float32 if plan[0] == J.KERNEL_PLAIN_X2 else torch.float64
     for T in (1, 2):
         got = _gpu(shape, 13, dt, T, plan)
         assert np.array_equal(got, _expected(shape, 13, dt, T)), (shape, T)

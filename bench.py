@@ -37,6 +37,15 @@ M_S_FALLBACK = 6800.0  # GB/s, used only if MEASURED_PEAKS.json is absent
 # 2 FP64 lanes per SM per clock (1.25e12 / (2 * 152 * 2.07e9)).
 FP64_LANES_PER_SM_CLK = 2
 SMS = 152
+# Temporally blocked pass used for the comparison line: depth, tile bx x by,
+# z chunk, ring depth.
+BLOCKED_REF = {"f64": (4, 64, 16, 64, 8), "f32": (4, 64, 32, 128, 4)}
+# DRAM bytes per LUP of one launch, from the ncu captures summarised under
+# profiles/ (same kernel build): (kernel, dtype) -> (bytes per LUP, summary).
+MEASURED_TRAFFIC = {
+    ("plain_pass_kernel", "f64"): (15.89, "profiles/plain_pass_fp64_512cubed.md"),
+    ("plain_x2_kernel", "f32"): (7.75, "profiles/plain_x2_fp32_512cubed.md"),
+}
 SM_MAX_MHZ = 2070.0
 
 WORKLOADS = {
@@ -304,6 +313,11 @@ def run_ours(args, w):
                       J.KERNEL_PLAIN_X2: "plain_x2_kernel"}[plan["kernel"]]
     roof["avg_launch_ms"] = pass_ms
     roof["sm_mhz_during"] = clk
+    measured = MEASURED_TRAFFIC.get((roof["kernel"], w["dtype"]))
+    if measured is not None:
+        # bytes per LUP of the captured launch x the LUPs of one launch here
+        roof["traffic"] = measured[0] * lup_launch
+        roof["traffic_source"] = measured[1] + " (DRAM bytes per LUP scaled to this launch)"
 
     p0 = m_s / (2.0 * es)  # Eq. (2) for element size es
     line = {
@@ -323,21 +337,29 @@ def run_ours(args, w):
     if tune_glups is not None:
         line["tuner_best_glups"] = tune_glups
 
-    # ---- plain single-pass baseline kernel (blocked vs plain), untimed in value
+    # ---- comparison kernels, untimed in value: the scalar single-pass kernel
+    # (code balance of Eq. (2)) and a temporally blocked pass of fixed depth
     if rank == 0 and not args.no_plain:
-        hp = J.Handle(nx, ny, nz, dt)
-        J.jacobi_set_plan(hp, J.KERNEL_PLAIN)
-        Tp = min(T, 20)
-        J.jacobi_sweep(hp, A, B, Tp, stream)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        J.jacobi_sweep(hp, A, B, Tp, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        gp = nx * ny * nz * Tp / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        def glups_of(kernel, *fields):
+            hp = J.Handle(nx, ny, nz, dt)
+            J.jacobi_set_plan(hp, kernel, *fields)
+            Tp = min(T, 20)
+            J.jacobi_sweep(hp, A, B, Tp, stream)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            J.jacobi_sweep(hp, A, B, Tp, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            hp.close()
+            return nx * ny * nz * Tp / (e0.elapsed_time(e1) * 1e-3) / 1e9, Tp
+        gp, Tp = glups_of(J.KERNEL_PLAIN)
         line["plain"] = {"value": gp, "unit": "GLUP/s", "sweeps": Tp, "per_pass_frac": gp / p0}
-        line["blocked_vs_plain"] = (value / ws) / gp
-        hp.close()
+        line["tuned_vs_plain"] = (value / ws) / gp
+        bd = BLOCKED_REF[w["dtype"]]
+        gb, Tb = glups_of(J.KERNEL_TB, *bd)
+        line["blocked"] = {"value": gb, "unit": "GLUP/s", "sweeps": Tb,
+                           "plan": dict(zip(("depth", "bx", "by", "bz", "ring"), bd)),
+                           "hbm_bytes_per_lup_ideal": 2.0 * es / bd[0]}
 
     # ---- end to end through the host-buffer entry point
     if not args.no_e2e:
@@ -518,6 +540,8 @@ def run_poisson(args, w):
         J.jacobi_refine(H, u, f, hg, 1e-10, w["T"], 400)
     torch.cuda.synchronize()
     times, outers = [], []
+    J.jacobi_profile_enable(H, True)
+    J.jacobi_profile_read(H)
     for _ in range(args.steps):
         u.zero_()
         torch.cuda.synchronize()
@@ -527,6 +551,7 @@ def run_poisson(args, w):
         outers.append(outer)
         assert st == 0
     t_ref = statistics.median(times)
+    launches = J.jacobi_profile_read(H)["other_launches"]
     inner_lups = float(n ** 3) * w["T"] * outers[-1]
     # plain FP64 Jacobi to the same residual: chunks of 2000 sweeps
     u.zero_()
@@ -550,6 +575,7 @@ def run_poisson(args, w):
         "plain_fp64_jacobi": {"seconds": t_plain, "sweeps": sweeps, "final_rel": rel_p,
                               "glups": float(n ** 3) * sweeps / t_plain / 1e9},
         "speedup_refine_vs_plain_fp64": t_plain / t_ref,
+        "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -175,8 +175,9 @@ int jacobi_check_addition(unsigned long long count, unsigned long long seed,
 int jacobi_get_status(jacobi_h h, int *device_status);
 
 /* Kernel timing for benchmarks.  While enabled, every pass-kernel launch of
- * this handle is bracketed by two CUDA events recorded on the launch
- * stream, and every other kernel launch is counted.  enable = 0 stops
+ * this handle's sweeps is bracketed by two CUDA events recorded on the
+ * launch stream, and every other kernel launch of the handle (halo copies,
+ * and the Poisson and refinement kernels) is counted.  enable = 0 stops
  * recording (already recorded launches stay until read). */
 int jacobi_profile_enable(jacobi_h h, int enable);
 

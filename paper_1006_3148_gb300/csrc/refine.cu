@@ -145,6 +145,7 @@ int ensure_inner(jacobi_plan_s *h, int dtype, int T)
 int read_norm(jacobi_plan_s *h, cudaStream_t s, double *out)
 {
     reduce_partials_kernel<<<1, 32, 0, s>>>(h->partials, kRedBlocks, h->partials + kRedBlocks);
+    if (h->prof) h->prof_other += 1;
     cudaError_t e = cudaMemcpyAsync(h->h_sum, h->partials + kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return JACOBI_ERR_CUDA;
@@ -158,6 +159,7 @@ int residual_norm(jacobi_plan_s *h, const double *u, const double *f, float *g, 
     const double h2 = hgrid * hgrid;
     residual_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(u, f, g, h->nx, h->ny, h->nz, h2, 1.0 / h2, h->partials);
     if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
+    if (h->prof) h->prof_other += 1;
     return read_norm(h, s, rnorm);
 }
 
@@ -165,6 +167,7 @@ int f_norm(jacobi_plan_s *h, const double *f, cudaStream_t s, double *fnorm)
 {
     sumsq_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(f, h->nx, h->ny, h->nz, h->partials);
     if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
+    if (h->prof) h->prof_other += 1;
     return read_norm(h, s, fnorm);
 }
 
@@ -220,6 +223,7 @@ int jacobi_poisson_jacobi(jacobi_h h, void *u, void *tmp, const void *f, double 
     scale_kernel<<<608, 256, 0, s>>>(static_cast<const double *>(f), static_cast<double *>(h->g), hgrid * hgrid,
                                      h->nx, h->ny, h->nz);
     if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
+    if (h->prof) h->prof_other += 3;  // scale, then the sweep graph's halo and persistent kernels
     void *A[1] = {u}, *B[1] = {tmp};
     const void *G[1] = {h->g};
     return jacobi_batch_run_rhs(h->inner, A, B, G, stream);
@@ -263,6 +267,7 @@ int jacobi_refine(jacobi_h h, double *u, const double *f, double hgrid, double r
         const float *e = static_cast<const float *>((inner_sweeps % 2 == 0) ? h->e0 : h->e1);
         update_kernel<<<608, 256, 0, s>>>(u, e, h->nx, h->ny, h->nz);
         if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
+        if (h->prof) h->prof_other += 3;  // the sweep graph's halo and persistent kernels, update
         ++outer;
     }
     int dev_status = 0;

@@ -30,6 +30,7 @@ struct PlainArgs {
     const void *src;
     void *dst;
     int nx, ny, nz;
+    const void *rhs = nullptr;  // source term g: (sum + g) / 6, or nullptr
     int kz;      // planes per thread
     int tx, ty;  // CTA shape in cells
     int gy, gz;  // row blocks, z chunks (set by plain_launch)
@@ -88,8 +89,9 @@ struct jacobi_plan_s {
     void *e0 = nullptr, *e1 = nullptr;  // FP32 correction grids
     double *partials = nullptr;  // per-block partial sums of squares
     double *h_sum = nullptr;     // pinned host mirror of one reduced sum
-    jacobi_batch_h inner = nullptr;  // one-grid persistent sweep engine
-    int inner_dtype = -1, inner_T = -1;
+    cudaGraphExec_t inner_exec = nullptr;  // K single-pass sweeps with a source term
+    int inner_dtype = -1, inner_K = -1;
+    const void *inner_A = nullptr, *inner_B = nullptr, *inner_G = nullptr;
 };
 
 namespace jac {

@@ -5,14 +5,16 @@
 //   jacobi_refine            mixed-precision iterative refinement: FP64
 //                            residual and update, FP32 inner Jacobi sweeps on
 //                            the correction
-// The inner sweeps (and the plain FP64 Jacobi) run on the persistent batch
-// engine with one grid: hundreds of dependent sweeps of a small grid in one
-// launch, each tile waiting only on its neighbours (no launch per sweep).
+// The inner sweeps (and the plain FP64 Jacobi) are single-pass sweep
+// kernels with the source term, replayed from a CUDA graph of K sweeps: a
+// small grid stays in L2 and each sweep costs one kernel, with no host
+// launch per sweep.
 // Sums of squares are reduced in a fixed order (per-thread grid-stride
 // order, then a fixed tree per block, then the block partials in index
 // order), so results do not depend on timing.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "jacobi_internal.h"
@@ -121,23 +123,100 @@ int ensure_common(jacobi_plan_s *h)
     return JACOBI_OK;
 }
 
-// One-grid persistent engine with T sweeps of the given dtype on this grid.
-int ensure_inner(jacobi_plan_s *h, int dtype, int T)
+// Launch shape of the single-pass sweep kernel for this grid: two x cells
+// per thread for FP32 grids of even nx (the FP64 form gains nothing on an
+// FP64-pipe-bound sweep), 32 x 8 threads, and the most planes per thread
+// (8, 4, 2, 1) that still leaves about two waves of 2048 threads per SM.
+PlainArgs inner_args(const jacobi_plan_s *h, int dtype, const void *rhs, bool *x2)
 {
-    if (h->inner && h->inner_dtype == dtype && h->inner_T == T) return JACOBI_OK;
-    if (h->inner) jacobi_batch_destroy(h->inner);
-    h->inner = nullptr;
-    int st = jacobi_batch_create(&h->inner, 1, &h->nx, &h->ny, &h->nz, &dtype, &T);
-    if (st != JACOBI_OK) return st;
-    // small grid, many dependent sweeps: short tiles split in z give every
-    // SM work in each sweep
-    const long long cells_xy = (long long)h->nx * h->ny;
-    int bz = 0;
-    if (cells_xy * h->nz < (1ll << 24)) bz = 16;
-    st = jacobi_batch_set_tile(h->inner, 32, 4, bz);
-    if (st != JACOBI_OK) return st;
+    PlainArgs a;
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.nz = h->nz;
+    a.rhs = rhs;
+    a.tx = 32;
+    a.ty = 8;
+    *x2 = (dtype == JACOBI_F32 && h->nx % 2 == 0);
+    const long long row = *x2 ? 32ll * (((h->nx + 2) / 2 + 31) / 32) : 32ll * ((h->nx + 31) / 32);
+    const long long want = 2ll * std::max(h->sms, 1) * 2048;
+    a.kz = 1;
+    for (int kz : {8, 4, 2}) {
+        if (row * h->ny * ((h->nz + kz - 1) / kz) >= want) {
+            a.kz = kz;
+            break;
+        }
+    }
+    return a;
+}
+
+cudaError_t sweep_once(const jacobi_plan_s *h, int dtype, PlainArgs a, bool x2, const void *src, void *dst,
+                       cudaStream_t s)
+{
+    a.src = src;
+    a.dst = dst;
+    return x2 ? plain_x2_launch(dtype, a, s) : plain_launch(dtype, a, s);
+}
+
+// A graph of K sweeps A -> B -> A ... with source term G, cached on the
+// handle by (dtype, K, A, B, G).  K is even, so the graph leaves its result
+// in A and can be replayed.
+int ensure_inner(jacobi_plan_s *h, int dtype, int K, void *A, void *B, const void *G)
+{
+    if (h->inner_exec && h->inner_dtype == dtype && h->inner_K == K && h->inner_A == A && h->inner_B == B &&
+        h->inner_G == G)
+        return JACOBI_OK;
+    if (h->inner_exec) cudaGraphExecDestroy(h->inner_exec);
+    h->inner_exec = nullptr;
+    bool x2 = false;
+    const PlainArgs a = inner_args(h, dtype, G, &x2);
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return JACOBI_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int t = 0; t < K; ++t) {
+            const cudaError_t le = sweep_once(h, dtype, a, x2, (t % 2 == 0) ? A : B, (t % 2 == 0) ? B : A, cs);
+            if (le != cudaSuccess && e == cudaSuccess) e = le;
+        }
+        const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = ce;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->inner_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        h->inner_exec = nullptr;
+        return JACOBI_ERR_CUDA;
+    }
     h->inner_dtype = dtype;
-    h->inner_T = T;
+    h->inner_K = K;
+    h->inner_A = A;
+    h->inner_B = B;
+    h->inner_G = G;
+    return JACOBI_OK;
+}
+
+// T sweeps A -> B -> ... with source term G on stream s (halos of A and B
+// already equal): ceil(T/512) replays of a graph of K ~ T/ceil(T/512) sweeps
+// (K even), then the few remaining sweeps launched one by one.  The result
+// is in B if T is odd, else in A.
+int run_inner(jacobi_plan_s *h, int dtype, int T, void *A, void *B, const void *G, cudaStream_t s)
+{
+    const int K = (T / ((T + 511) / 512)) & ~1;
+    int done = 0;
+    if (K >= 2) {
+        const int st = ensure_inner(h, dtype, K, A, B, G);
+        if (st != JACOBI_OK) return st;
+        for (; done + K <= T; done += K)
+            if (cudaGraphLaunch(h->inner_exec, s) != cudaSuccess) return JACOBI_ERR_CUDA;
+    }
+    bool x2 = false;
+    const PlainArgs a = inner_args(h, dtype, G, &x2);
+    for (int t = done; t < T; ++t)
+        if (sweep_once(h, dtype, a, x2, (t % 2 == 0) ? A : B, (t % 2 == 0) ? B : A, s) != cudaSuccess)
+            return JACOBI_ERR_CUDA;
+    if (h->prof) h->prof_other += T;
     return JACOBI_OK;
 }
 
@@ -180,11 +259,11 @@ void free_poisson_scratch(jacobi_plan_s *h)
     if (h->e1) cudaFree(h->e1);
     if (h->partials) cudaFree(h->partials);
     if (h->h_sum) cudaFreeHost(h->h_sum);
-    if (h->inner) jacobi_batch_destroy(h->inner);
+    if (h->inner_exec) cudaGraphExecDestroy(h->inner_exec);
     h->g = h->e0 = h->e1 = nullptr;
     h->partials = nullptr;
     h->h_sum = nullptr;
-    h->inner = nullptr;
+    h->inner_exec = nullptr;
 }
 
 }  // namespace jac
@@ -218,15 +297,12 @@ int jacobi_poisson_jacobi(jacobi_h h, void *u, void *tmp, const void *f, double 
     if (sweeps == 0) return JACOBI_OK;
     cudaStream_t s = (cudaStream_t)stream;
     if (!h->g && cudaMalloc(&h->g, cells(h) * sizeof(double)) != cudaSuccess) return JACOBI_ERR_ALLOC;
-    int st = ensure_inner(h, JACOBI_F64, sweeps);
-    if (st != JACOBI_OK) return st;
     scale_kernel<<<608, 256, 0, s>>>(static_cast<const double *>(f), static_cast<double *>(h->g), hgrid * hgrid,
                                      h->nx, h->ny, h->nz);
     if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
-    if (h->prof) h->prof_other += 3;  // scale, then the sweep graph's halo and persistent kernels
-    void *A[1] = {u}, *B[1] = {tmp};
-    const void *G[1] = {h->g};
-    return jacobi_batch_run_rhs(h->inner, A, B, G, stream);
+    if (halo_copy_launch(JACOBI_F64, u, tmp, h->nx, h->ny, h->nz, s) != cudaSuccess) return JACOBI_ERR_CUDA;
+    if (h->prof) h->prof_other += 2;  // scale, halo copy
+    return run_inner(h, JACOBI_F64, sweeps, u, tmp, h->g, s);
 }
 
 int jacobi_refine(jacobi_h h, double *u, const double *f, double hgrid, double rel_tol, int inner_sweeps,
@@ -244,8 +320,6 @@ int jacobi_refine(jacobi_h h, double *u, const double *f, double hgrid, double r
     if (!h->g && cudaMalloc(&h->g, n * sizeof(double)) != cudaSuccess) return JACOBI_ERR_ALLOC;
     if (!h->e0 && cudaMalloc(&h->e0, n * sizeof(float)) != cudaSuccess) return JACOBI_ERR_ALLOC;
     if (!h->e1 && cudaMalloc(&h->e1, n * sizeof(float)) != cudaSuccess) return JACOBI_ERR_ALLOC;
-    st = ensure_inner(h, JACOBI_F32, inner_sweeps);
-    if (st != JACOBI_OK) return st;
 
     double fn = 0.0;
     st = f_norm(h, f, s, &fn);
@@ -260,20 +334,15 @@ int jacobi_refine(jacobi_h h, double *u, const double *f, double hgrid, double r
         if (rel <= rel_tol || outer >= max_outer) break;
         if (cudaMemsetAsync(h->e0, 0, n * sizeof(float), s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (cudaMemsetAsync(h->e1, 0, n * sizeof(float), s) != cudaSuccess) return JACOBI_ERR_CUDA;
-        void *A[1] = {h->e0}, *B[1] = {h->e1};
-        const void *G[1] = {h->g};
-        st = jacobi_batch_run_rhs(h->inner, A, B, G, stream);
+        // zero correction and zero halo, then the FP32 sweeps on it
+        st = run_inner(h, JACOBI_F32, inner_sweeps, h->e0, h->e1, h->g, s);
         if (st != JACOBI_OK) return st;
         const float *e = static_cast<const float *>((inner_sweeps % 2 == 0) ? h->e0 : h->e1);
         update_kernel<<<608, 256, 0, s>>>(u, e, h->nx, h->ny, h->nz);
         if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
-        if (h->prof) h->prof_other += 3;  // the sweep graph's halo and persistent kernels, update
+        if (h->prof) h->prof_other += 1;  // update
         ++outer;
     }
-    int dev_status = 0;
-    st = jacobi_batch_get_status(h->inner, &dev_status);
-    if (st != JACOBI_OK) return st;
-    if (dev_status != 0) return dev_status;
     if (outer_done) *outer_done = outer;
     if (final_rel_residual) *final_rel_residual = rel;
     return rel <= rel_tol ? JACOBI_OK : JACOBI_ERR_NOT_CONVERGED;

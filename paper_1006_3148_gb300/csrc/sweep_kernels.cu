@@ -83,8 +83,10 @@ __global__ void fill_kernel(T *p, long long n, T v)
 // ----------------------------------------------------------------- plain
 // One sweep per launch.  Thread (i, j) walks kz planes of its column with the
 // values at k-1, k, k+1 in registers; the four in-plane neighbours come from
-// global memory (mostly L1 hits: neighbouring threads load them too).
-template <typename T>
+// global memory (mostly L1 hits: neighbouring threads load them too).  RHS:
+// a source term g (same layout as the grid) is added to the neighbour sum
+// before the division, (sum + g) / 6 (the Poisson sweeps).
+template <typename T, bool RHS>
 __global__ void __launch_bounds__(1024) plain_pass_kernel(const PlainArgs a)
 {
     // (row block, z chunk) pairs are numbered t = yb + gy * zc and spread
@@ -103,12 +105,18 @@ __global__ void __launch_bounds__(1024) plain_pass_kernel(const PlainArgs a)
     const long long c0 = kb * plane + j * NXP + i;
     const T *__restrict__ p = static_cast<const T *>(a.src) + c0;
     T *__restrict__ q = static_cast<T *>(a.dst) + c0;
+    const T *__restrict__ g = RHS ? static_cast<const T *>(a.rhs) + c0 : nullptr;
     const int nxp = a.nx + 2;
     T lo = __ldg(p - plane), mid = __ldg(p);
 #pragma unroll 4
     for (int k = kb; k < ke; ++k) {
         const T hi = __ldg(p + plane);
-        *q = Arith<T>::update(__ldg(p - 1), __ldg(p + 1), __ldg(p - nxp), __ldg(p + nxp), lo, hi);
+        if (RHS) {
+            *q = Arith<T>::update_rhs(__ldg(p - 1), __ldg(p + 1), __ldg(p - nxp), __ldg(p + nxp), lo, hi, __ldg(g));
+            g += plane;
+        } else {
+            *q = Arith<T>::update(__ldg(p - 1), __ldg(p + 1), __ldg(p - nxp), __ldg(p + nxp), lo, hi);
+        }
         lo = mid;
         mid = hi;
         p += plane;
@@ -140,6 +148,16 @@ struct Pair<float> {
         s = __fadd2_rn(s, hi);
         return __fmul2_rn(s, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
     }
+    static __device__ __forceinline__ V update_rhs(float w, V mid, float e, V ym, V yp, V lo, V hi, V g)
+    {
+        V s = __fadd2_rn(make_float2(w, mid.x), make_float2(mid.y, e));
+        s = __fadd2_rn(s, ym);
+        s = __fadd2_rn(s, yp);
+        s = __fadd2_rn(s, lo);
+        s = __fadd2_rn(s, hi);
+        s = __fadd2_rn(s, g);
+        return __fmul2_rn(s, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+    }
 };
 template <>
 struct Pair<double> {
@@ -151,9 +169,16 @@ struct Pair<double> {
         o.y = Arith<double>::update(mid.x, e, ym.y, yp.y, lo.y, hi.y);
         return o;
     }
+    static __device__ __forceinline__ V update_rhs(double w, V mid, double e, V ym, V yp, V lo, V hi, V g)
+    {
+        V o;
+        o.x = Arith<double>::update_rhs(w, mid.y, ym.x, yp.x, lo.x, hi.x, g.x);
+        o.y = Arith<double>::update_rhs(mid.x, e, ym.y, yp.y, lo.y, hi.y, g.y);
+        return o;
+    }
 };
 
-template <typename T>
+template <typename T, bool RHS>
 __global__ void __launch_bounds__(1024) plain_x2_kernel(const PlainArgs a)
 {
     using V = typename Pair<T>::V;
@@ -174,6 +199,7 @@ __global__ void __launch_bounds__(1024) plain_x2_kernel(const PlainArgs a)
     const T *__restrict__ p = static_cast<const T *>(a.src) + c0;
     const V *__restrict__ p2 = reinterpret_cast<const V *>(p);
     V *__restrict__ q2 = reinterpret_cast<V *>(static_cast<T *>(a.dst) + c0);
+    const V *__restrict__ g2 = RHS ? reinterpret_cast<const V *>(static_cast<const T *>(a.rhs) + c0) : nullptr;
     const long long P2 = plane >> 1, R2 = NXP >> 1;  // plane and row in pairs
     V zero;
     zero.x = T(0);
@@ -182,10 +208,11 @@ __global__ void __launch_bounds__(1024) plain_x2_kernel(const PlainArgs a)
     V lo = live ? __ldg(p2 - P2) : zero, mid = live ? __ldg(p2) : zero;
 #pragma unroll 4
     for (int k = kb; k < ke; ++k) {
-        V hi = zero, ym = zero, yp = zero;
+        V hi = zero, ym = zero, yp = zero, gv = zero;
         T w = T(0), e = T(0);
         if (live) {
             hi = __ldg(p2 + P2);
+            if (RHS) gv = __ldg(g2);
             ym = __ldg(p2 - R2);
             yp = __ldg(p2 + R2);
             // Cells beyond the pair at the warp's ends.  For pair 0 the cell
@@ -198,7 +225,7 @@ __global__ void __launch_bounds__(1024) plain_x2_kernel(const PlainArgs a)
         const T er = __shfl_down_sync(0xffffffffu, mid.x, 1);
         if (lane != 0) w = wl;
         if (lane != 31) e = er;
-        V o = Pair<T>::update(w, mid, e, ym, yp, lo, hi);
+        V o = RHS ? Pair<T>::update_rhs(w, mid, e, ym, yp, lo, hi, gv) : Pair<T>::update(w, mid, e, ym, yp, lo, hi);
         if (left_halo) o.x = mid.x;
         if (right_halo) o.y = mid.y;
         if (live) *q2 = o;
@@ -206,6 +233,7 @@ __global__ void __launch_bounds__(1024) plain_x2_kernel(const PlainArgs a)
         mid = hi;
         p2 += P2;
         q2 += P2;
+        if (RHS) g2 += P2;
         p += plane;
     }
 }
@@ -748,8 +776,13 @@ cudaError_t plain_launch(int dtype, PlainArgs a, cudaStream_t s)
     if (bz > 65535) return cudaErrorInvalidConfiguration;
     dim3 block((unsigned)a.tx, (unsigned)a.ty, 1);
     dim3 grid((unsigned)((a.nx + a.tx - 1) / a.tx), (unsigned)by, (unsigned)bz);
-    if (dtype == JACOBI_F64) plain_pass_kernel<double><<<grid, block, 0, s>>>(a);
-    else plain_pass_kernel<float><<<grid, block, 0, s>>>(a);
+    if (dtype == JACOBI_F64) {
+        if (a.rhs) plain_pass_kernel<double, true><<<grid, block, 0, s>>>(a);
+        else plain_pass_kernel<double, false><<<grid, block, 0, s>>>(a);
+    } else {
+        if (a.rhs) plain_pass_kernel<float, true><<<grid, block, 0, s>>>(a);
+        else plain_pass_kernel<float, false><<<grid, block, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -763,8 +796,13 @@ cudaError_t plain_x2_launch(int dtype, PlainArgs a, cudaStream_t s)
     const int npairs = (a.nx + 2) / 2;
     dim3 block((unsigned)a.tx, (unsigned)a.ty, 1);
     dim3 grid((unsigned)((npairs + a.tx - 1) / a.tx), (unsigned)by, (unsigned)bz);
-    if (dtype == JACOBI_F64) plain_x2_kernel<double><<<grid, block, 0, s>>>(a);
-    else plain_x2_kernel<float><<<grid, block, 0, s>>>(a);
+    if (dtype == JACOBI_F64) {
+        if (a.rhs) plain_x2_kernel<double, true><<<grid, block, 0, s>>>(a);
+        else plain_x2_kernel<double, false><<<grid, block, 0, s>>>(a);
+    } else {
+        if (a.rhs) plain_x2_kernel<float, true><<<grid, block, 0, s>>>(a);
+        else plain_x2_kernel<float, false><<<grid, block, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

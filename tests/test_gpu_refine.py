@@ -30,6 +30,37 @@ def test_plain_fp64_poisson_jacobi_bit_exact():
         assert np.array_equal(out.cpu().numpy(), exp), sweeps
 
 
+def test_plain_fp64_poisson_jacobi_graph_replays_and_tail_bit_exact():
+    # 1025 sweeps: two replays of a 512-sweep graph, then one launch
+    nx, ny, nz = 9, 7, 6
+    h = 1.0 / 10.0
+    f = inputs.normal_rhs(nx, ny, nz, seed=19)
+    u0 = inputs.uniform_grid(nx, ny, nz, seed=20)
+    H = J.Handle(nx, ny, nz, torch.float64)
+    u = u0.cuda()
+    tmp = torch.full_like(u, float("nan"))
+    out = J.jacobi_poisson_jacobi(H, u, tmp, f.cuda(), h, 1025)
+    torch.cuda.synchronize()
+    exp = oracle.poisson_jacobi(u0.numpy().copy(), f.numpy(), h, 1025)
+    assert out is tmp and np.array_equal(out.cpu().numpy(), exp)
+
+
+@pytest.mark.parametrize("n", [15, 16])
+def test_refine_outer_steps_match_oracle_odd_and_even_nx(n):
+    # odd nx runs the scalar FP32 sweep, even nx the two-cells-per-thread one.
+    # The residual's 1/h^2 product (the oracle divides by h^2) may move the
+    # last bits of the source term, so the outer counts may differ by one.
+    h = 1.0 / (n + 1)
+    f = inputs.normal_rhs(n, n - 1, n - 2, seed=21)
+    H = J.Handle(n, n - 1, n - 2, torch.float64)
+    u = torch.zeros_like(f).cuda()
+    st, outer, rel = J.jacobi_refine(H, u, f.cuda(), h, 1e-10, 60, 100)
+    st_o, outer_o, rel_o = oracle.refine(np.zeros_like(f.numpy()), f.numpy(), h, 1e-10, 60, 100)
+    assert st == 0 and st_o == 0 and abs(outer - outer_o) <= 1 and rel <= 1e-10
+    uh = u.cpu().numpy()
+    assert oracle.norm2(oracle.poisson_residual(uh, f.numpy(), h)) / oracle.norm2(f.numpy()) <= 1.01e-10
+
+
 def test_residual_matches_oracle():
     nx, ny, nz = 20, 18, 16
     h = 1.0 / 21.0

@@ -252,13 +252,18 @@ int jacobi_poisson_residual_noalloc(const void *u, const void *f, int nx, int ny
 
 /* ---------------------------------------------------------------- batch
  * Many independent grids (each its own size, element type and sweep count
- * T_g) swept in ONE persistent kernel launch that a CUDA graph replays.
- * Work items are (grid, x-y tile column, sweep), taken in pass-major order
- * from a device-side queue; an item waits (bounded) until its tile and the
- * four face-neighbour tiles finished the previous sweep -- per-tile
- * progress counters, the counters c_i of the relaxed synchronisation of
- * Sect. 2.2.  Each grid ends exactly as after jacobi_sweep with T_g sweeps:
- * result in B_g if T_g is odd, else in A_g. */
+ * T_g), swept by a CUDA graph that one of two engines builds:
+ *   JACOBI_BATCH_SWEEPS (default): one kernel launch per sweep covers every
+ *     grid, one CTA per (grid, row block, z chunk) unit; FP64 and FP32
+ *     units are dealt out alternately so both kinds share the SMs.
+ *   JACOBI_BATCH_PERSISTENT: ONE persistent launch.  Work items are (grid,
+ *     x-y tile column, sweep), taken in pass-major order from a device-side
+ *     queue; an item waits (bounded) until its tile and the face-neighbour
+ *     tiles finished the previous sweep -- per-tile progress counters, the
+ *     counters c_i of the relaxed synchronisation of Sect. 2.2.
+ * Each grid ends exactly as after jacobi_sweep with T_g sweeps: result in
+ * B_g if T_g is odd, else in A_g. */
+enum { JACOBI_BATCH_PERSISTENT = 0, JACOBI_BATCH_SWEEPS = 1 };
 
 /* Creates a batch of n (1..65535) grids; nx/ny/nz/dtype/T are host arrays
  * of n entries (sizes >= 1, dtype JACOBI_F64/F32, T >= 0, each grid below
@@ -285,14 +290,24 @@ int jacobi_batch_run_rhs(jacobi_batch_h b, void *const *A, void *const *B, const
 /* Frees the batch (after the caller synchronised its streams). */
 int jacobi_batch_destroy(jacobi_batch_h b);
 
-/* Tile of a work item: bx*by cells (bx*by <= 4096) of bz planes (bz = 0:
- * the whole z column; bz > 0 also splits z, and an item then also waits on
- * the tiles above and below).  Re-captures the graph. */
+/* Selects the persistent engine with a work-item tile of bx*by cells
+ * (bx*by <= 4096) and bz planes (bz = 0: the whole z column; bz > 0 also
+ * splits z, and an item then also waits on the tiles above and below).
+ * Re-captures the graph. */
 int jacobi_batch_set_tile(jacobi_batch_h b, int bx, int by, int bz);
+
+/* Selects the engine (JACOBI_BATCH_*); kz > 0 sets the sweep engine's
+ * planes per thread (0 keeps the current value, initially 16).  Re-captures
+ * the graph.  JACOBI_ERR_ARG for an unknown engine or kz < 0. */
+int jacobi_batch_set_engine(jacobi_batch_h b, int engine, int kz);
+
+/* Current engine and sweep-engine planes per thread (either may be NULL). */
+int jacobi_batch_get_engine(jacobi_batch_h b, int *engine, int *kz);
 
 /* Autotuner for the batch: fills the caller's scratch grids (arrays of n
  * device pointers, same shapes as the batch) with a constant, times the
- * candidate tiles and keeps the fastest.  Synchronises stream. */
+ * sweep engine at several planes per thread and the persistent engine at
+ * several tiles, and keeps the fastest.  Synchronises stream. */
 int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scratchB,
                       jacobi_stream_t stream, double *glups);
 
@@ -304,7 +319,8 @@ int jacobi_batch_get_status(jacobi_batch_h b, int *device_status);
 
 /* Test hook: mode 1 makes the persistent kernel never publish sweep 2 of
  * the first tile, so that dependent waits run out after limit_ms and the
- * kernel records JACOBI_ERR_TIMEOUT (no fault); re-captures the graph. */
+ * kernel records JACOBI_ERR_TIMEOUT (no fault); re-captures the graph.
+ * Mode 1 needs the persistent engine (else JACOBI_ERR_UNSUPPORTED). */
 int jacobi_batch_debug_set_fault(jacobi_batch_h b, int mode, int limit_ms);
 
 #ifdef __cplusplus

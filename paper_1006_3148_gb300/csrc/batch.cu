@@ -1,6 +1,16 @@
 // Batched sweeps: many independent grids of different sizes and element
-// types, all T_g sweeps of all grids in ONE persistent launch, replayed from
-// a CUDA graph.
+// types, replayed from a CUDA graph by one of two engines.
+//
+// Sweep engine (JACOBI_BATCH_SWEEPS): one launch per sweep p covers every
+// grid, one CTA per (grid, run of 256 x-y cells, z chunk) unit running the
+// single-pass column walk; kernel boundaries order the sweeps, so no CTA
+// waits on another.  The runs follow the row-major order of the interior
+// cells of a plane, so warps stay full whatever nx is (an FP64 warp
+// instruction costs the same with idle lanes).  Units of FP64 and FP32 grids are dealt out alternately, so that
+// FP64-pipe-bound and HBM-bound CTAs share the SMs.
+//
+// Persistent engine (JACOBI_BATCH_PERSISTENT): all T_g sweeps of all grids
+// in ONE persistent launch.
 //
 // Work items are (grid g, tile t of g, sweep p), numbered pass-major:
 // item = p * total_tiles + (tile_base[g] + t).  Resident CTAs take items
@@ -35,7 +45,17 @@ struct BatchGrid {
     int nx, ny, nz, dtype, T;
     int ntx, nty, ntz;
     int tile_base;  // global index of this grid's tile 0
+    int nbxy, nbz;  // sweep engine: runs of kSweepThreads x-y cells, z chunks
 };
+
+// Sweep engine: grid g's units are numbered from unit_base within the list
+// of grids of its dtype (FP64 list first in the table, then FP32).
+struct SweepEntry {
+    long long unit_base;
+    int grid;
+};
+
+constexpr int kSweepThreads = 256;  // CTA of the sweep engine
 
 struct BatchArgs {
     const BatchGrid *grids;
@@ -167,6 +187,78 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs a)
     }
 }
 
+// Sweep p of every grid with T_g > p.  Block b takes, while both lists have
+// units left, alternately a unit of the FP64 list (even b) and of the FP32
+// list (odd b); then the rest of the longer list.
+template <typename T, bool RHS>
+__device__ __forceinline__ void sweep_unit(const BatchGrid &G, int u, int p, int kz)
+{
+    const int r = u % G.nbxy, zc = u / G.nbxy;
+    const int c = r * kSweepThreads + threadIdx.x;  // row-major interior cell of the plane
+    if (c >= G.nx * G.ny) return;
+    const int i = 1 + c % G.nx, j = 1 + c / G.nx;
+    const long long NXP = G.nx + 2, plane = NXP * (G.ny + 2);
+    const int kb = 1 + zc * kz;
+    const int ke = (G.nz + 1 - kb < kz) ? G.nz + 1 : kb + kz;
+    const long long c0 = kb * plane + j * NXP + i;
+    const T *__restrict__ q0 = static_cast<const T *>((p % 2 == 0) ? G.A : G.B) + c0;
+    T *__restrict__ q = static_cast<T *>((p % 2 == 0) ? G.B : G.A) + c0;
+    const T *__restrict__ g = RHS ? static_cast<const T *>(G.rhs) + c0 : nullptr;
+    const int nxp = G.nx + 2;
+    T lo = __ldg(q0 - plane), mid = __ldg(q0);
+#pragma unroll 4
+    for (int k = kb; k < ke; ++k) {
+        const T hi = __ldg(q0 + plane);
+        if (RHS) {
+            *q = Arith<T>::update_rhs(__ldg(q0 - 1), __ldg(q0 + 1), __ldg(q0 - nxp), __ldg(q0 + nxp), lo, hi, __ldg(g));
+            g += plane;
+        } else {
+            *q = Arith<T>::update(__ldg(q0 - 1), __ldg(q0 + 1), __ldg(q0 - nxp), __ldg(q0 + nxp), lo, hi);
+        }
+        lo = mid;
+        mid = hi;
+        q0 += plane;
+        q += plane;
+    }
+}
+
+__global__ void __launch_bounds__(kSweepThreads) batch_sweep_kernel(const BatchGrid *grids,
+                                                                         const SweepEntry *tab, int n64, int n32,
+                                                                         long long u64, long long u32, int p, int kz)
+{
+    const long long b = blockIdx.x + (long long)gridDim.x * blockIdx.y;
+    const long long m = u64 < u32 ? u64 : u32;
+    int list;
+    long long idx;
+    if (b < 2 * m) {
+        list = (int)(b & 1);
+        idx = b >> 1;
+    } else {
+        list = (u64 > u32) ? 0 : 1;
+        idx = b - m;
+    }
+    if (idx >= (list == 0 ? u64 : u32)) return;
+    const SweepEntry *t = tab + (list == 0 ? 0 : n64);
+    int lo = 0, hi = (list == 0 ? n64 : n32) - 1;  // last entry with unit_base <= idx
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t[mid].unit_base <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchGrid &G = grids[t[lo].grid];
+    if (p >= G.T) return;
+    const int u = (int)(idx - t[lo].unit_base);
+    // element type and source term are uniform per block: the plane loop is
+    // instantiated for each combination
+    if (list == 0) {
+        if (G.rhs) sweep_unit<double, true>(G, u, p, kz);
+        else sweep_unit<double, false>(G, u, p, kz);
+    } else {
+        if (G.rhs) sweep_unit<float, true>(G, u, p, kz);
+        else sweep_unit<float, false>(G, u, p, kz);
+    }
+}
+
 // Copies the halo of A into B for every grid (blockIdx.y = grid).
 __global__ void batch_halo_kernel(const BatchGrid *grids)
 {
@@ -192,6 +284,11 @@ using namespace jac;
 struct jacobi_batch_s {
     int n = 0;
     std::vector<BatchGrid> grids;  // host copy (pointers bound by jacobi_batch_run)
+    int engine = JACOBI_BATCH_SWEEPS;
+    int kz = 16;                   // sweep engine: planes per thread
+    SweepEntry *d_tab = nullptr;   // sweep engine: FP64 list, then FP32 list
+    int n64 = 0, n32 = 0;
+    long long u64 = 0, u32 = 0;    // units per list
     int bx = 32, by = 8, bz = 0;  // bz 0: whole z column per item
     int total_tiles = 0, max_T = 0;
     long long total_items = 0;
@@ -223,6 +320,38 @@ void layout(jacobi_batch_s *b)
     }
     b->total_tiles = base;
     b->total_items = (long long)base * b->max_T;
+    b->n64 = b->n32 = 0;
+    b->u64 = b->u32 = 0;
+    for (BatchGrid &G : b->grids) {
+        G.nbxy = (G.nx * G.ny + kSweepThreads - 1) / kSweepThreads;
+        G.nbz = (G.nz + b->kz - 1) / b->kz;
+        const long long units = (long long)G.nbxy * G.nbz;
+        if (G.dtype == JACOBI_F64) {
+            ++b->n64;
+            b->u64 += units;
+        } else {
+            ++b->n32;
+            b->u32 += units;
+        }
+    }
+}
+
+// Sweep-engine table: FP64 grids in order with their unit bases, then the
+// FP32 grids.
+std::vector<SweepEntry> sweep_table(const jacobi_batch_s *b)
+{
+    std::vector<SweepEntry> t;
+    t.reserve((size_t)b->n);
+    for (int pass = 0; pass < 2; ++pass) {
+        long long base = 0;
+        for (int g = 0; g < b->n; ++g) {
+            const BatchGrid &G = b->grids[(size_t)g];
+            if ((G.dtype == JACOBI_F64) != (pass == 0)) continue;
+            t.push_back(SweepEntry{base, g});
+            base += (long long)G.nbxy * G.nbz;
+        }
+    }
+    return t;
 }
 
 void free_graph(jacobi_batch_s *b)
@@ -266,15 +395,34 @@ int build_graph(jacobi_batch_s *b)
     a.limit_ns = b->limit_ns;
     a.fault_mode = b->fault_mode;
 
+    if (b->engine == JACOBI_BATCH_SWEEPS) {
+        const std::vector<SweepEntry> tab = sweep_table(b);
+        if (b->d_tab) cudaFree(b->d_tab);
+        b->d_tab = nullptr;
+        e = cudaMalloc(&b->d_tab, sizeof(SweepEntry) * (size_t)b->n);
+        if (e != cudaSuccess) return JACOBI_ERR_ALLOC;
+        e = cudaMemcpy(b->d_tab, tab.data(), sizeof(SweepEntry) * (size_t)b->n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return JACOBI_ERR_CUDA;
+    }
+    const long long units = b->u64 + b->u32;
+    const unsigned gx = (unsigned)std::min<long long>(units, 1ll << 30);
+    const unsigned gy = (unsigned)((units + gx - 1) / gx);
     cudaStream_t cs;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return JACOBI_ERR_CUDA;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaMemsetAsync(b->d_ctl, 0, sizeof(int), cs);
-        cudaMemsetAsync(b->d_ctl + 2, 0, sizeof(int) * (size_t)b->total_tiles, cs);
-        batch_halo_kernel<<<dim3(64, (unsigned)b->n), 256, 0, cs>>>(b->d_grids);
-        batch_kernel<<<b->persistent_blocks, 256, 0, cs>>>(a);
+        if (b->engine == JACOBI_BATCH_SWEEPS) {
+            batch_halo_kernel<<<dim3(64, (unsigned)b->n), 256, 0, cs>>>(b->d_grids);
+            for (int p = 0; p < b->max_T; ++p)
+                batch_sweep_kernel<<<dim3(gx, gy), kSweepThreads, 0, cs>>>(
+                    b->d_grids, b->d_tab, b->n64, b->n32, b->u64, b->u32, p, b->kz);
+        } else {
+            cudaMemsetAsync(b->d_ctl, 0, sizeof(int), cs);
+            cudaMemsetAsync(b->d_ctl + 2, 0, sizeof(int) * (size_t)b->total_tiles, cs);
+            batch_halo_kernel<<<dim3(64, (unsigned)b->n), 256, 0, cs>>>(b->d_grids);
+            batch_kernel<<<b->persistent_blocks, 256, 0, cs>>>(a);
+        }
         e = cudaStreamEndCapture(cs, &b->graph);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -326,6 +474,7 @@ int jacobi_batch_create(jacobi_batch_h *out, int n, const int *nx, const int *ny
     if (st != JACOBI_OK) {
         cudaFree(b->d_grids);
         if (b->d_ctl) cudaFree(b->d_ctl);
+        if (b->d_tab) cudaFree(b->d_tab);
         delete b;
         return st;
     }
@@ -339,6 +488,7 @@ int jacobi_batch_destroy(jacobi_batch_h b)
     free_graph(b);
     if (b->d_grids) cudaFree(b->d_grids);
     if (b->d_ctl) cudaFree(b->d_ctl);
+    if (b->d_tab) cudaFree(b->d_tab);
     delete b;
     return JACOBI_OK;
 }
@@ -372,11 +522,29 @@ int jacobi_batch_run(jacobi_batch_h b, void *const *A, void *const *B, jacobi_st
 int jacobi_batch_set_tile(jacobi_batch_h b, int bx, int by, int bz)
 {
     if (!b || bx < 1 || by < 1 || bz < 0 || bx * by > 4096) return JACOBI_ERR_ARG;
+    b->engine = JACOBI_BATCH_PERSISTENT;
     b->bx = bx;
     b->by = by;
     b->bz = bz;
     layout(b);
     return build_graph(b);
+}
+
+int jacobi_batch_set_engine(jacobi_batch_h b, int engine, int kz)
+{
+    if (!b || (engine != JACOBI_BATCH_PERSISTENT && engine != JACOBI_BATCH_SWEEPS) || kz < 0) return JACOBI_ERR_ARG;
+    b->engine = engine;
+    if (kz > 0) b->kz = kz;
+    layout(b);
+    return build_graph(b);
+}
+
+int jacobi_batch_get_engine(jacobi_batch_h b, int *engine, int *kz)
+{
+    if (!b) return JACOBI_ERR_ARG;
+    if (engine) *engine = b->engine;
+    if (kz) *kz = b->kz;
+    return JACOBI_OK;
 }
 
 int jacobi_batch_get_info(jacobi_batch_h b, int *bx, int *by, int *bz, long long *items, int *blocks)
@@ -405,6 +573,7 @@ int jacobi_batch_get_status(jacobi_batch_h b, int *device_status)
 int jacobi_batch_debug_set_fault(jacobi_batch_h b, int mode, int limit_ms)
 {
     if (!b || mode < 0 || mode > 1 || limit_ms < 1) return JACOBI_ERR_ARG;
+    if (mode == 1 && b->engine != JACOBI_BATCH_PERSISTENT) return JACOBI_ERR_UNSUPPORTED;
     b->fault_mode = mode;
     b->limit_ns = (unsigned long long)limit_ms * 1000000ull;
     return build_graph(b);
@@ -424,7 +593,12 @@ int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scra
     }
     double lups = 0.0;
     for (const BatchGrid &G : b->grids) lups += (double)G.nx * G.ny * G.nz * G.T;
-    const int tiles[][3] = {{32, 4, 0}, {32, 8, 0}, {32, 16, 0}, {64, 4, 0}, {64, 8, 0}, {128, 2, 0}, {32, 8, 64}};
+    // candidates: {engine, bx, by, bz or kz}
+    const int cands[][4] = {{JACOBI_BATCH_SWEEPS, 0, 0, 8},  {JACOBI_BATCH_SWEEPS, 0, 0, 16},
+                            {JACOBI_BATCH_SWEEPS, 0, 0, 32}, {JACOBI_BATCH_PERSISTENT, 32, 4, 0},
+                            {JACOBI_BATCH_PERSISTENT, 32, 8, 0}, {JACOBI_BATCH_PERSISTENT, 32, 16, 0},
+                            {JACOBI_BATCH_PERSISTENT, 64, 4, 0}, {JACOBI_BATCH_PERSISTENT, 64, 8, 0},
+                            {JACOBI_BATCH_PERSISTENT, 128, 2, 0}, {JACOBI_BATCH_PERSISTENT, 32, 8, 64}};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return JACOBI_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -432,9 +606,17 @@ int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scra
         return JACOBI_ERR_CUDA;
     }
     double best = -1.0;
-    int bbx = b->bx, bby = b->by, bbz = b->bz, st = JACOBI_OK;
-    for (const auto &t : tiles) {
-        st = jacobi_batch_set_tile(b, t[0], t[1], t[2]);
+    int beng = b->engine, bkz = b->kz, bbx = b->bx, bby = b->by, bbz = b->bz, st = JACOBI_OK;
+    for (const auto &t : cands) {
+        if (t[0] == JACOBI_BATCH_SWEEPS) {
+            b->bx = bbx;
+            b->by = bby;
+            b->bz = bbz;
+            st = jacobi_batch_set_engine(b, t[0], t[3]);
+        } else {
+            b->engine = t[0];
+            st = jacobi_batch_set_tile(b, t[1], t[2], t[3]);
+        }
         if (st != JACOBI_OK) break;
         st = jacobi_batch_run(b, scratchA, scratchB, stream);  // warm-up
         if (st != JACOBI_OK) break;
@@ -451,16 +633,27 @@ int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scra
         const double g = lups / (ms * 1e-3) / 1e9;
         if (g > best) {
             best = g;
-            bbx = t[0];
-            bby = t[1];
-            bbz = t[2];
+            beng = t[0];
+            if (t[0] == JACOBI_BATCH_SWEEPS) {
+                bkz = t[3];
+            } else {
+                bbx = t[1];
+                bby = t[2];
+                bbz = t[3];
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != JACOBI_OK) return st;
     if (glups) *glups = best;
-    return jacobi_batch_set_tile(b, bbx, bby, bbz);
+    b->engine = beng;
+    b->kz = bkz;
+    b->bx = bbx;
+    b->by = bby;
+    b->bz = bbz;
+    layout(b);
+    return build_graph(b);
 }
 
 }  // extern "C"

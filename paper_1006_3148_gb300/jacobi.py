@@ -18,6 +18,7 @@ from . import build as _build
 F64 = 0
 F32 = 1
 KERNEL_AUTO, KERNEL_PLAIN, KERNEL_TB, KERNEL_PLAIN_X2 = 0, 1, 2, 3
+BATCH_PERSISTENT, BATCH_SWEEPS = 0, 1
 
 STATUS = {
     0: "JACOBI_OK", -1: "JACOBI_ERR_ARG", -2: "JACOBI_ERR_DTYPE", -3: "JACOBI_ERR_ALLOC",
@@ -78,6 +79,8 @@ def load(build_if_missing: bool = True):
             "jacobi_batch_run": ([P, ctypes.POINTER(P), ctypes.POINTER(P), P], i),
             "jacobi_batch_destroy": ([P], i),
             "jacobi_batch_set_tile": ([P, i, i, i], i),
+            "jacobi_batch_set_engine": ([P, i, i], i),
+            "jacobi_batch_get_engine": ([P, pi, pi], i),
             "jacobi_batch_run_rhs": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P], i),
             "jacobi_batch_tune": ([P, ctypes.POINTER(P), ctypes.POINTER(P), P, ctypes.POINTER(d)], i),
             "jacobi_batch_get_info": ([P, pi, pi, pi, ctypes.POINTER(ctypes.c_longlong), pi], i),
@@ -304,6 +307,16 @@ def jacobi_batch_destroy(b: Batch):
 
 def jacobi_batch_set_tile(b: Batch, bx: int, by: int, bz: int = 0):
     _check(load().jacobi_batch_set_tile(b.ptr, int(bx), int(by), int(bz)), "jacobi_batch_set_tile")
+
+
+def jacobi_batch_set_engine(b: Batch, engine: int, kz: int = 0):
+    _check(load().jacobi_batch_set_engine(b.ptr, int(engine), int(kz)), "jacobi_batch_set_engine")
+
+
+def jacobi_batch_get_engine(b: Batch) -> dict:
+    e, kz = ctypes.c_int(), ctypes.c_int()
+    _check(load().jacobi_batch_get_engine(b.ptr, ctypes.byref(e), ctypes.byref(kz)), "jacobi_batch_get_engine")
+    return {"engine": e.value, "kz": kz.value}
 
 
 def jacobi_batch_run_rhs(b: Batch, A, B, RHS, stream=None):

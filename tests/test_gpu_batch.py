@@ -1,5 +1,5 @@
-"""GPU parity of the batched persistent sweep (one launch, CUDA graph)
-against the CPU oracle, grid by grid."""
+"""GPU parity of the batched sweeps (CUDA graph; sweep-per-launch engine and
+persistent engine) against the CPU oracle, grid by grid."""
 import numpy as np
 import pytest
 import torch
@@ -19,7 +19,7 @@ def _make(dims, f32, seed):
     return hosts
 
 
-def _check(b, hosts, Ts, tol_fp64=True):
+def _check(b, hosts, Ts, tol_fp64=True, expected=None):
     A = [h.cuda() for h in hosts]
     B = [torch.full_like(x, float("nan")) for x in A]
     outs = J.jacobi_batch_run(b, A, B)
@@ -27,7 +27,7 @@ def _check(b, hosts, Ts, tol_fp64=True):
     assert J.jacobi_batch_get_status(b) == 0
     for g, (h, T) in enumerate(zip(hosts, Ts)):
         got = outs[g].cpu().numpy()
-        exp = oracle.jacobi_result(h.numpy(), T)
+        exp = expected[g] if expected is not None else oracle.jacobi_result(h.numpy(), T)
         assert np.array_equal(got, exp), (g, h.dtype, T)
         if h.dtype == torch.float32 and tol_fp64:
             e64 = oracle.jacobi_result(h.to(torch.float64).numpy(), T)
@@ -45,6 +45,70 @@ def test_small_mixed_batch_all_tiles():
     for tile in [(32, 8), (4, 2), (1, 1), (64, 4), (7, 3), (8, 4, 3), (16, 2, 1)]:
         J.jacobi_batch_set_tile(b, *tile)
         _check(b, hosts, Ts)
+    b.close()
+
+
+@pytest.mark.parametrize("kz", [1, 3, 8, 64])
+def test_small_mixed_batch_sweep_engine(kz):
+    rng = np.random.default_rng(5)
+    n = 17
+    dims = [tuple(int(v) for v in rng.integers(1, 40, size=3)) for _ in range(n)]
+    f32 = [bool(v) for v in rng.integers(0, 2, size=n)]
+    Ts = [int(v) for v in rng.integers(0, 9, size=n)]
+    hosts = _make(dims, f32, 60)
+    b = J.Batch(dims, [torch.float32 if f else torch.float64 for f in f32], Ts)
+    J.jacobi_batch_set_engine(b, J.BATCH_SWEEPS, kz)
+    assert J.jacobi_batch_get_engine(b) == {"engine": J.BATCH_SWEEPS, "kz": kz}
+    _check(b, hosts, Ts)
+    b.close()
+
+
+def test_single_dtype_batches_sweep_engine():
+    for dt in (torch.float64, torch.float32):
+        dims = [(9, 33, 5), (40, 3, 17), (1, 1, 1)]
+        Ts = [4, 7, 2]
+        hosts = _make(dims, [dt == torch.float32] * 3, 80)
+        b = J.Batch(dims, [dt] * 3, Ts)
+        J.jacobi_batch_set_engine(b, J.BATCH_SWEEPS, 4)
+        _check(b, hosts, Ts)
+        b.close()
+
+
+def test_batch_source_term_both_engines():
+    # Poisson form: FP64 grids with g = h^2 f against the oracle's plain FP64
+    # Jacobi with a source; one grid without a source term
+    dims = [(12, 10, 9), (7, 15, 6), (20, 4, 11)]
+    Ts = [6, 5, 3]
+    hg = [1.0 / 11.0, 1.0 / 16.0, 1.0 / 21.0]
+    fs = [inputs.normal_rhs(*d, seed=30 + g) for g, d in enumerate(dims)]
+    us = [inputs.uniform_grid(*d, seed=40 + g) for g, d in enumerate(dims)]
+    exp = [oracle.poisson_jacobi(us[g].numpy().copy(), fs[g].numpy(), hg[g], Ts[g]) for g in range(2)]
+    exp.append(oracle.jacobi_result(us[2].numpy(), Ts[2]))
+    b = J.Batch(dims, [torch.float64] * 3, Ts)
+    for engine in (J.BATCH_SWEEPS, J.BATCH_PERSISTENT):
+        if engine == J.BATCH_SWEEPS:
+            J.jacobi_batch_set_engine(b, engine, 4)
+        else:
+            J.jacobi_batch_set_tile(b, 8, 4)
+        A = [u.cuda() for u in us]
+        B = [torch.full_like(x, float("nan")) for x in A]
+        R = [(hg[g] * hg[g] * fs[g]).cuda() for g in range(2)] + [None]
+        outs = J.jacobi_batch_run_rhs(b, A, B, R)
+        torch.cuda.synchronize()
+        for g in range(3):
+            assert np.array_equal(outs[g].cpu().numpy(), exp[g]), (engine, g)
+    b.close()
+
+
+def test_engine_selection_and_errors():
+    b = J.Batch([(8, 8, 8)], [torch.float64], [2])
+    assert J.jacobi_batch_get_engine(b)["engine"] == J.BATCH_SWEEPS
+    L = J.load()
+    assert L.jacobi_batch_set_engine(b.ptr, 7, 0) == -1
+    assert L.jacobi_batch_set_engine(b.ptr, J.BATCH_SWEEPS, -1) == -1
+    assert L.jacobi_batch_debug_set_fault(b.ptr, 1, 50) == -9  # hook needs the persistent engine
+    J.jacobi_batch_set_tile(b, 8, 8)
+    assert J.jacobi_batch_get_engine(b)["engine"] == J.BATCH_PERSISTENT
     b.close()
 
 
@@ -82,4 +146,8 @@ def test_batch_workload_256_grids_32_to_192():
     b = J.Batch(dims, [torch.float32 if f else torch.float64 for f in f32], Ts)
     info = J.jacobi_batch_get_info(b)
     assert info["items"] > 0 and info["blocks"] > 0 and info["bz"] == 0
-    _check(b, hosts, Ts)
+    exp = [oracle.jacobi_result(h.numpy(), T) for h, T in zip(hosts, Ts)]
+    assert J.jacobi_batch_get_engine(b)["engine"] == J.BATCH_SWEEPS
+    _check(b, hosts, Ts, expected=exp)
+    J.jacobi_batch_set_tile(b, 32, 8)  # the persistent engine, same results
+    _check(b, hosts, Ts, tol_fp64=False, expected=exp)

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "arith.cuh"
+#include "grid.cuh"
 #include "jacobi_internal.h"
 #include "ptx.cuh"
 
@@ -264,14 +265,11 @@ __global__ void batch_halo_kernel(const BatchGrid *grids)
 {
     const BatchGrid G = grids[blockIdx.y];
     if (G.T <= 0) return;
-    const long long NXP = G.nx + 2, NYP = G.ny + 2, NZP = G.nz + 2;
-    const long long total = NXP * NYP * NZP;
-    const int es = G.dtype == JACOBI_F64 ? 8 : 4;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long x = i % NXP, y = (i / NXP) % NYP, z = i / (NXP * NYP);
-        if (x != 0 && x != NXP - 1 && y != 0 && y != NYP - 1 && z != 0 && z != NZP - 1) continue;
-        if (es == 8) static_cast<double *>(G.B)[i] = static_cast<const double *>(G.A)[i];
+    const long long total = halo_count(G.nx, G.ny, G.nz);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long i = halo_cell(t, G.nx, G.ny, G.nz);
+        if (G.dtype == JACOBI_F64) static_cast<double *>(G.B)[i] = static_cast<const double *>(G.A)[i];
         else static_cast<float *>(G.B)[i] = static_cast<const float *>(G.A)[i];
     }
 }

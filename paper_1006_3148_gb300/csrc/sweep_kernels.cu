@@ -25,6 +25,7 @@
 #include <type_traits>
 
 #include "arith.cuh"
+#include "grid.cuh"
 #include "jacobi_internal.h"
 #include "ptx.cuh"
 
@@ -39,35 +40,10 @@ __device__ __forceinline__ void record_error(int *status, int code)
 template <typename T>
 __global__ void halo_copy_kernel(const T *__restrict__ A, T *__restrict__ B, int nx, int ny, int nz)
 {
-    const long long NXP = nx + 2, NYP = ny + 2;
-    const long long nzf = 2 * NXP * NYP;          // k = 0 and k = nz+1 planes
-    const long long nyf = 2 * NXP * (long long)nz;  // j = 0 and j = ny+1 rows
-    const long long nxf = 2 * (long long)ny * nz;   // i = 0 and i = nx+1 cells
-    const long long total = nzf + nyf + nxf;
+    const long long total = halo_count(nx, ny, nz);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        long long i, j, k;
-        if (t < nzf) {
-            const long long p = t % (NXP * NYP);
-            k = (t < NXP * NYP) ? 0 : nz + 1;
-            j = p / NXP;
-            i = p % NXP;
-        } else if (t < nzf + nyf) {
-            const long long u = t - nzf;
-            const long long half = NXP * nz;
-            j = (u < half) ? 0 : ny + 1;
-            const long long p = u % half;
-            k = 1 + p / NXP;
-            i = p % NXP;
-        } else {
-            const long long u = t - nzf - nyf;
-            const long long half = (long long)ny * nz;
-            i = (u < half) ? 0 : nx + 1;
-            const long long p = u % half;
-            k = 1 + p / ny;
-            j = 1 + p % ny;
-        }
-        const long long idx = (k * NYP + j) * NXP + i;
+        const long long idx = halo_cell(t, nx, ny, nz);
         B[idx] = A[idx];
     }
 }
@@ -808,8 +784,7 @@ cudaError_t plain_x2_launch(int dtype, PlainArgs a, cudaStream_t s)
 
 cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, int nz, cudaStream_t s)
 {
-    const long long NXP = nx + 2, NYP = ny + 2;
-    const long long total = 2 * NXP * NYP + 2 * NXP * (long long)nz + 2 * (long long)ny * nz;
+    const long long total = halo_count(nx, ny, nz);
     const int block = 256;
     const long long want = (total + block - 1) / block;
     const unsigned grid = (unsigned)std::min<long long>(want, 152 * 16);

@@ -245,7 +245,7 @@ def run_ours(args, w):
         f = args.plan.split(":")
         ring = int(f[5]) if len(f) > 5 else 0
         threads = int(f[6]) if len(f) > 6 else 0
-        J.jacobi_set_plan(h, {"tb": J.KERNEL_TB, "plain": J.KERNEL_PLAIN, "x2": J.KERNEL_PLAIN_X2}[f[0]], int(f[1]), int(f[2]), int(f[3]),
+        J.jacobi_set_plan(h, {"tb": J.KERNEL_TB, "plain": J.KERNEL_PLAIN, "x2": J.KERNEL_PLAIN_X2, "cta": J.KERNEL_TB_CTA}[f[0]], int(f[1]), int(f[2]), int(f[3]),
                           int(f[4]), ring, threads)
     elif not args.no_tune:
         sa, sb = torch.empty_like(A), torch.empty_like(A)
@@ -310,7 +310,7 @@ def run_ours(args, w):
         roof = {"bound": "hbm", "achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
                 "traffic": None, "peak_source": peak_src}
     roof["kernel"] = {J.KERNEL_TB: "tb_pass_kernel", J.KERNEL_PLAIN: "plain_pass_kernel",
-                      J.KERNEL_PLAIN_X2: "plain_x2_kernel"}[plan["kernel"]]
+                      J.KERNEL_PLAIN_X2: "plain_x2_kernel", J.KERNEL_TB_CTA: "tbc_pass_kernel"}[plan["kernel"]]
     roof["avg_launch_ms"] = pass_ms
     roof["sm_mhz_during"] = clk
     measured = MEASURED_TRAFFIC.get((roof["kernel"], w["dtype"]))
@@ -596,7 +596,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fp64_512", choices=sorted(WORKLOADS))
-    ap.add_argument("--plan", default=None, help="force a plan kernel:depth:bx:by:bz[:ring[:threads]], kernel tb, plain or x2, e.g. tb:4:64:16:64:8 or x2:1:32:8:16")
+    ap.add_argument("--plan", default=None, help="force a plan kernel:depth:bx:by:bz[:ring[:threads]], kernel tb, cta, plain or x2, e.g. tb:4:64:16:64:8, cta:4:64:32:64:0:512 or x2:1:32:8:16")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -63,9 +63,12 @@ enum {
                                 global memory: the single-pass baseline       */
     JACOBI_KERNEL_TB = 2,    /* z-streaming pass; depth d > 1 runs the
                                 time-skewed cluster pipeline                  */
-    JACOBI_KERNEL_PLAIN_X2 = 3 /* single-pass kernel with two x cells per
+    JACOBI_KERNEL_PLAIN_X2 = 3, /* single-pass kernel with two x cells per
                                 thread (vector loads, shuffled x-neighbours,
                                 packed FP32 additions); even nx only          */
+    JACOBI_KERNEL_TB_CTA = 4 /* temporal blocking inside one CTA: depth 2..4
+                                levels applied to a tile's planes in shared
+                                memory (T updates per thread, Sect. 2.1)     */
 };
 
 typedef struct jacobi_plan_s *jacobi_h;
@@ -114,12 +117,15 @@ int jacobi_sweep_host(jacobi_h h, const void *A_host, void *out_host, int T,
  * memory), and threads = CTA width (128, 256 or 512; 0 = automatic).  The
  * ring depth is the pipeline looseness of Sect. 2.2 (a producer may run up
  * to ring planes ahead of its consumer; at least one plane, Eq. 3).
- * Depths > 8 need the non-portable cluster size.  For PLAIN and PLAIN_X2:
+ * Depths > 8 need the non-portable cluster size.  For TB_CTA: depth 2..4
+ * (a remainder pass of depth 1 runs the single-pass kernel), tile bx*by, z
+ * chunk bz, threads 256 or 512 (0 = 512), at most 8 cells of the widened
+ * tile (bx+2d)(by+2d) per thread; ring ignored.  For PLAIN and PLAIN_X2:
  * bx*by = CTA shape in threads (bx a multiple of 32, bx*by <= 1024; a
  * PLAIN_X2 thread covers two x cells) and bz = planes each thread walks in
  * z; ring and threads are ignored.  A zero bx, by or bz takes the family's
- * default (PLAIN 32 x 8 x 8; PLAIN_X2 32 x 8 x 16; TB 64 x 16 x 64, clamped
- * to the grid).  JACOBI_KERNEL_AUTO returns to the tuned/default plan.
+ * default (PLAIN 32 x 8 x 8; PLAIN_X2 32 x 8 x 16; TB 64 x 16 x 64; TB_CTA
+ * 64 x 32 x 64; tiles clamped to the grid).  JACOBI_KERNEL_AUTO returns to the tuned/default plan.
  * Returns JACOBI_ERR_ARG for out-of-range fields and JACOBI_ERR_UNSUPPORTED
  * if the plan cannot launch on this device (shared memory, registers,
  * cluster occupancy). */

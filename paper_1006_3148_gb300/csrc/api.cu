@@ -85,13 +85,15 @@ bool prof_event(jacobi_plan_s *h, cudaStream_t s)
 
 // Replaces zero tile fields of a forced plan by the kernel family's defaults
 // (PLAIN: 32 x 8 threads, 8 planes per thread; PLAIN_X2: 32 x 8 threads,
-// 16 planes; TB: 64 x 16 tile, 64 planes).
+// 16 planes; TB: 64 x 16 tile, 64 planes; TB_CTA: 64 x 32 tile, 64 planes,
+// 512 threads).
 Plan resolve_plan(const jacobi_plan_s *h, Plan p)
 {
     const bool plain = p.kernel == JACOBI_KERNEL_PLAIN || p.kernel == JACOBI_KERNEL_PLAIN_X2;
     if (p.bx == 0) p.bx = plain ? 32 : std::min(64, h->nx);
-    if (p.by == 0) p.by = plain ? 8 : std::min(16, h->ny);
+    if (p.by == 0) p.by = plain ? 8 : std::min(p.kernel == JACOBI_KERNEL_TB_CTA ? 32 : 16, h->ny);
     if (p.bz == 0) p.bz = plain ? (p.kernel == JACOBI_KERNEL_PLAIN_X2 ? 16 : 8) : std::min(64, h->nz);
+    if (p.kernel == JACOBI_KERNEL_TB_CTA && p.threads == 0) p.threads = 512;
     return p;
 }
 
@@ -105,6 +107,19 @@ int check_plan(const jacobi_plan_s *h, const Plan &p)
         // (row block, z chunk) pairs must fit grid y * grid z
         const long long pairs = (long long)((h->ny + p.by - 1) / p.by) * ((h->nz + p.bz - 1) / p.bz);
         return pairs <= 65535ll * 65535ll ? JACOBI_OK : JACOBI_ERR_UNSUPPORTED;
+    }
+    if (p.kernel == JACOBI_KERNEL_TB_CTA) {
+        if (p.depth < 2 || p.depth > 4 || p.bx < 1 || p.by < 1 || p.bz < 1) return JACOBI_ERR_ARG;
+        if (p.threads != 256 && p.threads != 512) return JACOBI_ERR_ARG;
+        TbcArgs a;
+        a.nx = h->nx;
+        a.ny = h->ny;
+        a.nz = h->nz;
+        size_t smem = 0;
+        const int st = tbc_configure(h->dtype, p.depth, p.bx, p.by, p.threads, &a, &smem);
+        if (st != JACOBI_OK) return st;
+        if ((h->ny + p.by - 1) / p.by > 65535 || (h->nz + p.bz - 1) / p.bz > 65535) return JACOBI_ERR_UNSUPPORTED;
+        return JACOBI_OK;
     }
     if (p.kernel != JACOBI_KERNEL_TB) return JACOBI_ERR_ARG;
     if (p.depth < 1 || p.depth > 16 || p.bx < 1 || p.by < 1 || p.bz < 1) return JACOBI_ERR_ARG;
@@ -150,6 +165,42 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
     std::vector<int> depths((size_t)T + 1);
     const int P = plan_passes(T, p.depth, depths.data(), T + 1);
     if (P < 0) return JACOBI_ERR_ARG;
+    if (p.kernel == JACOBI_KERNEL_TB_CTA) {
+        TbcArgs a;
+        a.nx = h->nx;
+        a.ny = h->ny;
+        a.nz = h->nz;
+        a.bz = p.bz;
+        PlainArgs pa;  // depth-1 passes of the plan: single-pass kernel
+        pa.nx = h->nx;
+        pa.ny = h->ny;
+        pa.nz = h->nz;
+        pa.tx = 32;
+        pa.ty = 8;
+        pa.kz = 16;
+        const bool x2 = h->dtype == JACOBI_F32 && h->nx % 2 == 0;
+        for (int q = 0; q < P; ++q) {
+            const void *src = (q % 2 == 0) ? A : B;
+            void *dst = (q % 2 == 0) ? B : A;
+            if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
+            if (depths[q] == 1) {
+                pa.src = src;
+                pa.dst = dst;
+                e = x2 ? plain_x2_launch(h->dtype, pa, s) : plain_launch(h->dtype, pa, s);
+            } else {
+                size_t smem = 0;
+                if (tbc_configure(h->dtype, depths[q], p.bx, p.by, p.threads, &a, &smem) != JACOBI_OK)
+                    return JACOBI_ERR_UNSUPPORTED;
+                a.src = src;
+                a.dst = dst;
+                e = tbc_launch(h->dtype, depths[q], p.threads, a, s);
+            }
+            if (e != cudaSuccess) return cuda_fail(e);
+            if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
+            if (h->prof) ++h->prof_pass;
+        }
+        return JACOBI_OK;
+    }
     TbArgs a;
     a.nx = h->nx;
     a.ny = h->ny;
@@ -315,7 +366,7 @@ int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, i
     p.bx = bx;
     p.by = by;
     p.bz = bz;
-    p.ring = plain ? 0 : ring;
+    p.ring = (plain || kernel == JACOBI_KERNEL_TB_CTA) ? 0 : ring;
     p.threads = plain ? 0 : threads;
     p = resolve_plan(h, p);
     const int st = check_plan(h, p);
@@ -492,6 +543,21 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
                 p.bz = kz;
                 consider(p);
             }
+    // Temporal blocking inside one CTA: depth x tile x CTA width x z chunk.
+    const int cta_tiles[][2] = {{32, 32}, {64, 24}, {64, 32}, {128, 16}};
+    for (int d = 2; d <= 4; ++d)
+        for (const auto &t : cta_tiles)
+            for (int nt : {256, 512})
+                for (int bz : {64, 128}) {
+                    Plan p;
+                    p.kernel = JACOBI_KERNEL_TB_CTA;
+                    p.depth = d;
+                    p.bx = t[0];
+                    p.by = t[1];
+                    p.bz = bz;
+                    p.threads = nt;
+                    consider(clampp(p));
+                }
     for (int di = 0; di < nd; ++di)
         for (const auto &t : tiles) {
             Plan p;

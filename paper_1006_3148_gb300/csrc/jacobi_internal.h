@@ -26,6 +26,15 @@ struct TbArgs {
     int fault_mode;     // test hook: 1 = drop one arrival (see jacobi.h)
 };
 
+// Arguments of one pass of the one-CTA temporally blocked kernel.
+struct TbcArgs {
+    const void *src;
+    void *dst;
+    int nx, ny, nz;
+    int bx, by, bz;  // tile interior (x, y) and z chunk
+    int W, H, WH;    // region: tile widened by the depth on each side
+};
+
 struct PlainArgs {
     const void *src;
     void *dst;
@@ -61,6 +70,11 @@ cudaError_t tb_configure(int dtype, int depth, int bx, int by, int ring, int thr
 cudaError_t tb_launch(int dtype, const TbArgs &a, const TbLaunch &L, cudaStream_t s);
 cudaError_t tb_max_clusters(int dtype, const TbLaunch &L, int depth, int *clusters);
 cudaError_t plain_launch(int dtype, PlainArgs a, cudaStream_t s);
+// One-CTA temporal blocking: checks a plan (depth 2..4, CTA of 256 or 512
+// threads, at most 8 cells per thread, shared memory) and fills the region
+// fields of a; launches one pass.
+int tbc_configure(int dtype, int depth, int bx, int by, int threads, TbcArgs *a, size_t *smem);
+cudaError_t tbc_launch(int dtype, int depth, int threads, const TbcArgs &a, cudaStream_t s);
 cudaError_t plain_x2_launch(int dtype, PlainArgs a, cudaStream_t s);  // nx even
 cudaError_t fill_launch(int dtype, void *p, long long n, double v, cudaStream_t s);
 cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, int nz, cudaStream_t s);

@@ -182,6 +182,18 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// Closes this thread's current group of cp.async operations; waits until at
+// most N of its groups are still pending.
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Wait for completion of the barrier phase with the given parity (acquire at
 // CTA scope: data that completed the phase through cp.async or st.async
 // transaction counts is visible to the waiting thread afterwards).  Gives up

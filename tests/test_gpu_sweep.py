@@ -64,6 +64,12 @@ PLANS = [
     (J.KERNEL_PLAIN, 1, 64, 4, 1),
     (J.KERNEL_PLAIN, 1, 128, 8, 3),
     (J.KERNEL_PLAIN, 1, 32, 32, 32),
+    (J.KERNEL_TB_CTA, 2, 8, 8, 8, 0, 256),
+    (J.KERNEL_TB_CTA, 3, 16, 8, 5, 0, 512),
+    (J.KERNEL_TB_CTA, 4, 32, 16, 16, 0, 512),
+    (J.KERNEL_TB_CTA, 4, 5, 7, 3, 0, 256),
+    (J.KERNEL_TB_CTA, 2, 64, 32, 64, 0, 512),
+    (J.KERNEL_TB_CTA, 4, 64, 32, 64, 0, 512),
 ]
 
 
@@ -77,7 +83,8 @@ def test_fp64_bit_exact_small(shape, plan):
 
 
 @pytest.mark.parametrize("shape", [(5, 4, 3), (33, 31, 29), (67, 45, 33)])
-@pytest.mark.parametrize("plan", [PLANS[0], PLANS[3], PLANS[6], PLANS[8]], ids=lambda p: "k%d_d%d" % p[:2])
+@pytest.mark.parametrize("plan", [PLANS[0], PLANS[3], PLANS[6], PLANS[8], PLANS[-1], PLANS[-4]],
+                         ids=lambda p: "k%d_d%d_%dx%d" % p[:4])
 def test_fp32_bitwise_vs_fp32_oracle_and_tolerance_vs_fp64(shape, plan):
     for T in (1, 4, 9):
         got = _gpu(shape, 12, torch.float32, T, plan)
@@ -92,7 +99,8 @@ def test_workload_64cubed_fp64_all_depths():
     # 64^3 interior, interior and halo U[0,1) from seed 1, T = 10
     shape = (64, 64, 64)
     exp = _expected(shape, 1, torch.float64, 10)
-    for plan in [None, (J.KERNEL_PLAIN, 1, 0, 0, 0)] + [(J.KERNEL_TB, d, 32, 16, 32) for d in (1, 2, 4, 8)]:
+    for plan in [None, (J.KERNEL_PLAIN, 1, 0, 0, 0)] + [(J.KERNEL_TB, d, 32, 16, 32) for d in (1, 2, 4, 8)] + \
+            [(J.KERNEL_TB_CTA, d, 32, 16, 24, 0, 512) for d in (2, 3, 4)]:
         got = _gpu(shape, 1, torch.float64, 10, plan)
         assert np.array_equal(got, exp), plan
 
@@ -129,6 +137,11 @@ def test_argument_errors():
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 1, 8, 8, 8, 5, 0) == -1
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 1, 8, 8, 8, 4, 96) == -1
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 8, 512, 512, 8, 0, 0) == -9
+    # TB_CTA: depth 2..4, 256 or 512 threads, at most 8 region cells per thread
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB_CTA, 5, 8, 8, 8, 0, 512) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB_CTA, 1, 8, 8, 8, 0, 512) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB_CTA, 2, 8, 8, 8, 0, 128) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB_CTA, 4, 128, 64, 8, 0, 256) == -9
     # PLAIN: CTA x extent a multiple of 32, at most 1024 threads, planes >= 0
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_PLAIN, 1, 48, 4, 8, 0, 0) == -1
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_PLAIN, 1, 64, 32, 8, 0, 0) == -1

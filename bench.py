@@ -37,9 +37,9 @@ M_S_FALLBACK = 6800.0  # GB/s, used only if MEASURED_PEAKS.json is absent
 # 2 FP64 lanes per SM per clock (1.25e12 / (2 * 152 * 2.07e9)).
 FP64_LANES_PER_SM_CLK = 2
 SMS = 152
-# Temporally blocked pass used for the comparison line: depth, tile bx x by,
-# z chunk, ring depth.
-BLOCKED_REF = {"f64": (4, 64, 16, 64, 8), "f32": (4, 64, 32, 128, 4)}
+# Temporally blocked pass used for the comparison line (one CTA applying d
+# levels): kernel, depth, tile bx x by, z chunk, ring (unused), threads.
+BLOCKED_REF = {"f64": (4, 4, 64, 32, 64, 0, 512), "f32": (4, 4, 32, 32, 128, 0, 256)}  # kernel TB_CTA
 # DRAM bytes per LUP of one launch, from the ncu captures summarised under
 # profiles/ (same kernel build): (kernel, dtype) -> (bytes per LUP, summary).
 MEASURED_TRAFFIC = {
@@ -356,10 +356,10 @@ def run_ours(args, w):
         line["plain"] = {"value": gp, "unit": "GLUP/s", "sweeps": Tp, "per_pass_frac": gp / p0}
         line["tuned_vs_plain"] = (value / ws) / gp
         bd = BLOCKED_REF[w["dtype"]]
-        gb, Tb = glups_of(J.KERNEL_TB, *bd)
+        gb, Tb = glups_of(*bd)
         line["blocked"] = {"value": gb, "unit": "GLUP/s", "sweeps": Tb,
-                           "plan": dict(zip(("depth", "bx", "by", "bz", "ring"), bd)),
-                           "hbm_bytes_per_lup_ideal": 2.0 * es / bd[0]}
+                           "plan": dict(zip(("kernel", "depth", "bx", "by", "bz", "ring", "threads"), bd)),
+                           "hbm_bytes_per_lup_ideal": 2.0 * es / bd[1]}
 
     # ---- end to end through the host-buffer entry point
     if not args.no_e2e:

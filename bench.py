@@ -41,10 +41,12 @@ SMS = 152
 # levels): kernel, depth, tile bx x by, z chunk, ring (unused), threads.
 BLOCKED_REF = {"f64": (4, 4, 64, 32, 64, 0, 512), "f32": (4, 4, 32, 32, 128, 0, 256)}  # kernel TB_CTA
 # DRAM bytes per LUP of one launch, from the ncu captures summarised under
-# profiles/ (same kernel build): (kernel, dtype) -> (bytes per LUP, summary).
+# profiles/ (same kernel build): (kernel, dtype, depth) -> (bytes per LUP,
+# summary).
 MEASURED_TRAFFIC = {
-    ("plain_pass_kernel", "f64"): (15.89, "profiles/plain_pass_fp64_512cubed.md"),
-    ("plain_x2_kernel", "f32"): (7.75, "profiles/plain_x2_fp32_512cubed.md"),
+    ("plain_pass_kernel", "f64", 1): (15.92, "profiles/plain_pass_fp64_512cubed.md"),
+    ("tbc4_pass_kernel", "f32", 2): (3.97, "profiles/tbc4_pass_fp32_d2_512cubed.md"),
+    ("tbc4_pass_kernel", "f32", 4): (2.04, "profiles/tbc4_pass_fp32_d4_512cubed.md"),
 }
 SM_MAX_MHZ = 2070.0
 
@@ -310,10 +312,11 @@ def run_ours(args, w):
         roof = {"bound": "hbm", "achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
                 "traffic": None, "peak_source": peak_src}
     roof["kernel"] = {J.KERNEL_TB: "tb_pass_kernel", J.KERNEL_PLAIN: "plain_pass_kernel",
-                      J.KERNEL_PLAIN_X2: "plain_x2_kernel", J.KERNEL_TB_CTA: "tbc_pass_kernel"}[plan["kernel"]]
+                      J.KERNEL_PLAIN_X2: "plain_x2_kernel",
+                      J.KERNEL_TB_CTA: "tbc4_pass_kernel" if w["dtype"] == "f32" else "tbc_pass_kernel"}[plan["kernel"]]
     roof["avg_launch_ms"] = pass_ms
     roof["sm_mhz_during"] = clk
-    measured = MEASURED_TRAFFIC.get((roof["kernel"], w["dtype"]))
+    measured = MEASURED_TRAFFIC.get((roof["kernel"], w["dtype"], plan["depth"]))
     if measured is not None:
         # bytes per LUP of the captured launch x the LUPs of one launch here
         roof["traffic"] = measured[0] * lup_launch

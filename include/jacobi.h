@@ -66,7 +66,7 @@ enum {
     JACOBI_KERNEL_PLAIN_X2 = 3, /* single-pass kernel with two x cells per
                                 thread (vector loads, shuffled x-neighbours,
                                 packed FP32 additions); even nx only          */
-    JACOBI_KERNEL_TB_CTA = 4 /* temporal blocking inside one CTA: depth 2..4
+    JACOBI_KERNEL_TB_CTA = 4 /* temporal blocking inside one CTA: depth 1..4
                                 levels applied to a tile's planes in shared
                                 memory (T updates per thread, Sect. 2.1)     */
 };
@@ -117,10 +117,11 @@ int jacobi_sweep_host(jacobi_h h, const void *A_host, void *out_host, int T,
  * memory), and threads = CTA width (128, 256 or 512; 0 = automatic).  The
  * ring depth is the pipeline looseness of Sect. 2.2 (a producer may run up
  * to ring planes ahead of its consumer; at least one plane, Eq. 3).
- * Depths > 8 need the non-portable cluster size.  For TB_CTA: depth 2..4
- * (a remainder pass of depth 1 runs the single-pass kernel), tile bx*by, z
- * chunk bz, threads 256 or 512 (0 = 512), at most 8 cells of the widened
- * tile (bx+2d)(by+2d) per thread; ring ignored.  For PLAIN and PLAIN_X2:
+ * Depths > 8 need the non-portable cluster size.  For TB_CTA: depth 1..4
+ * (1: one sweep per pass with the input planes staged in shared memory),
+ * tile bx*by, z chunk bz, threads 256 or 512 (0 = 512), at most 8 cells
+ * (FP64) or 4 quads of 4 cells (FP32) of the widened tile (bx+2d)(by+2d)
+ * per thread; ring ignored.  For PLAIN and PLAIN_X2:
  * bx*by = CTA shape in threads (bx a multiple of 32, bx*by <= 1024; a
  * PLAIN_X2 thread covers two x cells) and bz = planes each thread walks in
  * z; ring and threads are ignored.  A zero bx, by or bz takes the family's

@@ -109,7 +109,7 @@ int check_plan(const jacobi_plan_s *h, const Plan &p)
         return pairs <= 65535ll * 65535ll ? JACOBI_OK : JACOBI_ERR_UNSUPPORTED;
     }
     if (p.kernel == JACOBI_KERNEL_TB_CTA) {
-        if (p.depth < 2 || p.depth > 4 || p.bx < 1 || p.by < 1 || p.bz < 1) return JACOBI_ERR_ARG;
+        if (p.depth < 1 || p.depth > 4 || p.bx < 1 || p.by < 1 || p.bz < 1) return JACOBI_ERR_ARG;
         if (p.threads != 256 && p.threads != 512) return JACOBI_ERR_ARG;
         TbcArgs a;
         a.nx = h->nx;
@@ -171,30 +171,14 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
         a.ny = h->ny;
         a.nz = h->nz;
         a.bz = p.bz;
-        PlainArgs pa;  // depth-1 passes of the plan: single-pass kernel
-        pa.nx = h->nx;
-        pa.ny = h->ny;
-        pa.nz = h->nz;
-        pa.tx = 32;
-        pa.ty = 8;
-        pa.kz = 16;
-        const bool x2 = h->dtype == JACOBI_F32 && h->nx % 2 == 0;
         for (int q = 0; q < P; ++q) {
-            const void *src = (q % 2 == 0) ? A : B;
-            void *dst = (q % 2 == 0) ? B : A;
             if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
-            if (depths[q] == 1) {
-                pa.src = src;
-                pa.dst = dst;
-                e = x2 ? plain_x2_launch(h->dtype, pa, s) : plain_launch(h->dtype, pa, s);
-            } else {
-                size_t smem = 0;
-                if (tbc_configure(h->dtype, depths[q], p.bx, p.by, p.threads, &a, &smem) != JACOBI_OK)
-                    return JACOBI_ERR_UNSUPPORTED;
-                a.src = src;
-                a.dst = dst;
-                e = tbc_launch(h->dtype, depths[q], p.threads, a, s);
-            }
+            size_t smem = 0;
+            if (tbc_configure(h->dtype, depths[q], p.bx, p.by, p.threads, &a, &smem) != JACOBI_OK)
+                return JACOBI_ERR_UNSUPPORTED;
+            a.src = (q % 2 == 0) ? A : B;
+            a.dst = (q % 2 == 0) ? B : A;
+            e = tbc_launch(h->dtype, depths[q], p.threads, a, s);
             if (e != cudaSuccess) return cuda_fail(e);
             if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
             if (h->prof) ++h->prof_pass;
@@ -545,7 +529,7 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
             }
     // Temporal blocking inside one CTA: depth x tile x CTA width x z chunk.
     const int cta_tiles[][2] = {{32, 32}, {64, 24}, {64, 32}, {128, 16}};
-    for (int d = 2; d <= 4; ++d)
+    for (int d = 1; d <= 4; ++d)
         for (const auto &t : cta_tiles)
             for (int nt : {256, 512})
                 for (int bz : {64, 128}) {

@@ -69,8 +69,14 @@ struct TbLaunch {
 cudaError_t tb_configure(int dtype, int depth, int bx, int by, int ring, int threads, TbLaunch *out);
 cudaError_t tb_launch(int dtype, const TbArgs &a, const TbLaunch &L, cudaStream_t s);
 cudaError_t tb_max_clusters(int dtype, const TbLaunch &L, int depth, int *clusters);
+// Kernel entry of a cluster pass variant (threads, groups per thread), or
+// nullptr: parts 0/1 hold the FP64 variants, 2/3 the FP32 ones.
+const void *tb_kernel_part0(int nc, int maxg);
+const void *tb_kernel_part1(int nc, int maxg);
+const void *tb_kernel_part2(int nc, int maxg);
+const void *tb_kernel_part3(int nc, int maxg);
 cudaError_t plain_launch(int dtype, PlainArgs a, cudaStream_t s);
-// One-CTA temporal blocking: checks a plan (depth 2..4, CTA of 256 or 512
+// One-CTA temporal blocking: checks a plan (depth 1..4, CTA of 256 or 512
 // threads, at most 8 cells per thread, shared memory) and fills the region
 // fields of a; launches one pass.
 int tbc_configure(int dtype, int depth, int bx, int by, int threads, TbcArgs *a, size_t *smem);

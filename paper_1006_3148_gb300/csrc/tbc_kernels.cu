@@ -1,7 +1,8 @@
 // Temporal blocking inside one CTA (Sect. 2.1 with T updates per thread):
 // one CTA streams the planes of a tile widened by D cells on each side and
 // applies D time levels to them while they sit in shared memory, so each
-// pass reads the grid once and writes it once for D sweeps.
+// pass reads the grid once and writes it once for D sweeps.  D = 1 is the
+// plain sweep with every input plane staged once in shared memory.
 //
 // Step s of the z stream: level 1 updates plane s, level l plane s-l+1 (the
 // one-plane skew between consecutive levels plays the one-block shift of
@@ -325,6 +326,7 @@ template <int NT>
 cudaError_t launch_quad_depth(const TbcArgs &a, int depth, cudaStream_t s)
 {
     switch (depth) {
+    case 1: return launch_qpt<1, NT>(a, s);
     case 2: return launch_qpt<2, NT>(a, s);
     case 3: return launch_qpt<3, NT>(a, s);
     case 4: return launch_qpt<4, NT>(a, s);
@@ -360,6 +362,7 @@ template <typename T, int NT>
 cudaError_t launch_depth(const TbcArgs &a, int depth, cudaStream_t s)
 {
     switch (depth) {
+    case 1: return launch_cpt<T, 1, NT>(a, s);
     case 2: return launch_cpt<T, 2, NT>(a, s);
     case 3: return launch_cpt<T, 3, NT>(a, s);
     case 4: return launch_cpt<T, 4, NT>(a, s);
@@ -371,7 +374,7 @@ cudaError_t launch_depth(const TbcArgs &a, int depth, cudaStream_t s)
 
 int tbc_configure(int dtype, int depth, int bx, int by, int threads, TbcArgs *a, size_t *smem)
 {
-    if (depth < 2 || depth > 4 || bx < 1 || by < 1) return JACOBI_ERR_ARG;
+    if (depth < 1 || depth > 4 || bx < 1 || by < 1) return JACOBI_ERR_ARG;
     if ((long long)(a->nx + 2) * (a->ny + 2) >= (1ll << 31)) return JACOBI_ERR_UNSUPPORTED;  // 32-bit plane offsets
     if (threads != 256 && threads != 512) return JACOBI_ERR_ARG;
     a->bx = bx;

@@ -42,9 +42,10 @@ def _run(A0, plan):
 
 
 @pytest.mark.parametrize("plan", ["tuned", (J.KERNEL_TB_CTA, 4, 64, 32, 64, 0, 512), (J.KERNEL_TB_CTA, 3, 32, 32, 128, 0, 256),
+                                  (J.KERNEL_TB_CTA, 1, 64, 32, 64, 0, 512),
                                   (J.KERNEL_TB, 1, 64, 16, 64), (J.KERNEL_TB, 2, 64, 16, 64),
                                   (J.KERNEL_TB, 4, 64, 16, 128), (J.KERNEL_TB, 8, 32, 32, 128)],
-                         ids=["tuned", "cta_d4", "cta_d3", "d1", "d2", "d4", "d8"])
+                         ids=["tuned", "cta_d4", "cta_d3", "cta_d1", "d1", "d2", "d4", "d8"])
 def test_512cubed_fp64_bit_exact(c2, plan):
     A0, exp = c2
     got = _run(A0, plan)

@@ -70,6 +70,8 @@ PLANS = [
     (J.KERNEL_TB_CTA, 4, 5, 7, 3, 0, 256),
     (J.KERNEL_TB_CTA, 2, 64, 32, 64, 0, 512),
     (J.KERNEL_TB_CTA, 4, 64, 32, 64, 0, 512),
+    (J.KERNEL_TB_CTA, 1, 16, 8, 5, 0, 256),
+    (J.KERNEL_TB_CTA, 1, 64, 32, 64, 0, 512),
 ]
 
 
@@ -100,7 +102,7 @@ def test_workload_64cubed_fp64_all_depths():
     shape = (64, 64, 64)
     exp = _expected(shape, 1, torch.float64, 10)
     for plan in [None, (J.KERNEL_PLAIN, 1, 0, 0, 0)] + [(J.KERNEL_TB, d, 32, 16, 32) for d in (1, 2, 4, 8)] + \
-            [(J.KERNEL_TB_CTA, d, 32, 16, 24, 0, 512) for d in (2, 3, 4)]:
+            [(J.KERNEL_TB_CTA, d, 32, 16, 24, 0, 512) for d in (1, 2, 3, 4)]:
         got = _gpu(shape, 1, torch.float64, 10, plan)
         assert np.array_equal(got, exp), plan
 
@@ -137,9 +139,9 @@ def test_argument_errors():
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 1, 8, 8, 8, 5, 0) == -1
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 1, 8, 8, 8, 4, 96) == -1
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB, 8, 512, 512, 8, 0, 0) == -9
-    # TB_CTA: depth 2..4, 256 or 512 threads, at most 8 region cells per thread
+    # TB_CTA: depth 1..4, 256 or 512 threads, a bounded widened tile per thread
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB_CTA, 5, 8, 8, 8, 0, 512) == -1
-    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB_CTA, 1, 8, 8, 8, 0, 512) == -1
+    assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB_CTA, 0, 8, 8, 8, 0, 512) == -1
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB_CTA, 2, 8, 8, 8, 0, 128) == -1
     assert L.jacobi_set_plan(h.ptr, J.KERNEL_TB_CTA, 4, 128, 64, 8, 0, 256) == -9
     # PLAIN: CTA x extent a multiple of 32, at most 1024 threads, planes >= 0

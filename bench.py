@@ -43,6 +43,7 @@ BLOCKED_REF = {"f64": (4, 4, 64, 32, 64, 0, 512), "f32": (4, 4, 32, 32, 128, 0, 
 # DRAM bytes per LUP of one launch, from the ncu captures summarised under
 # profiles/ (same kernel build): (kernel, dtype, depth) -> (bytes per LUP,
 # summary).
+BATCH_SWEEP_TRAFFIC = (12.62, "profiles/batch_sweep_256grids.md (DRAM bytes per LUP, one sweep of the batch)")
 MEASURED_TRAFFIC = {
     ("plain_pass_kernel", "f64", 1): (15.92, "profiles/plain_pass_fp64_512cubed.md"),
     ("tbc4_pass_kernel", "f32", 2): (3.97, "profiles/tbc4_pass_fp32_d2_512cubed.md"),
@@ -477,6 +478,10 @@ def run_batch(args, w):
         roof = {"bound": "hbm", "achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
                 "traffic": None, "peak_source": peak_src}
     roof["kernel"] = "batch_sweep_kernel" if sweeps_engine else "batch_kernel"
+    if sweeps_engine:
+        # DRAM bytes per LUP of one sweep launch over the batch (ncu capture)
+        roof["traffic"] = BATCH_SWEEP_TRAFFIC[0] * lups / T
+        roof["traffic_source"] = BATCH_SWEEP_TRAFFIC[1]
     # the halo copy is ~1 % of a step; the rest is the sweep launches
     roof["avg_launch_ms"] = step_s * 1e3 / (T if sweeps_engine else 1)
     line = {

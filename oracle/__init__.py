@@ -55,6 +55,8 @@ def lib():
             build()
             L = ctypes.CDLL(_LIB)
             P, l, d = ctypes.c_void_p, ctypes.c_long, ctypes.c_double
+            L.oracle_set_threads.argtypes = [ctypes.c_int]
+            L.oracle_set_threads.restype = ctypes.c_int
             L.oracle_jacobi_f64.argtypes = [P, P, l, l, l, l]
             L.oracle_jacobi_f32.argtypes = [P, P, l, l, l, l]
             L.oracle_halo_copy_f64.argtypes = [P, P, l, l, l]
@@ -182,6 +184,12 @@ def poisson_dst(f, h: float) -> np.ndarray:
     u = np.zeros_like(f)
     u[1:-1, 1:-1, 1:-1] = idstn(fh / den, type=1)
     return u
+
+
+def set_threads(n: int) -> int:
+    """Sets the OpenMP threads of later oracle calls (results do not depend
+    on it); returns the number in effect."""
+    return int(lib().oracle_set_threads(int(n)))
 
 
 def threads() -> int:

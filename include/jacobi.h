@@ -126,8 +126,8 @@ int jacobi_sweep_host(jacobi_h h, const void *A_host, void *out_host, int T,
  * PLAIN_X2 thread covers two x cells) and bz = planes each thread walks in
  * z; ring and threads are ignored.  A zero bx, by or bz takes the family's
  * default (PLAIN 32 x 8 x 8; PLAIN_X2 32 x 8 x 16; TB 64 x 16 x 64; TB_CTA
- * 64 x 32 x 64; tiles clamped to the grid).  JACOBI_KERNEL_AUTO returns to the tuned/default plan.
- * Returns JACOBI_ERR_ARG for out-of-range fields and JACOBI_ERR_UNSUPPORTED
+ * 64 x 32 x 64; tiles clamped to the grid).  JACOBI_KERNEL_AUTO returns to
+ * the tuned/default plan.  Returns JACOBI_ERR_ARG for out-of-range fields and JACOBI_ERR_UNSUPPORTED
  * if the plan cannot launch on this device (shared memory, registers,
  * cluster occupancy). */
 int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, int ring,

@@ -32,6 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "GLUP/s (3D 7-pt Jacobi) and % of HBM roofline, blocked vs plain, 1×GB300"
+POISSON_METRIC = "time to relative residual 1e-10 (Poisson 96^3, refinement vs plain FP64 Jacobi)"
 M_S_FALLBACK = 6800.0  # GB/s, used only if MEASURED_PEAKS.json is absent
 # FP64 pipe of GB300: 1.25 TFLOP/s nominal counting an FMA as 2 flops, i.e.
 # 2 FP64 lanes per SM per clock (1.25e12 / (2 * 152 * 2.07e9)).
@@ -40,14 +41,14 @@ SMS = 152
 # Temporally blocked pass used for the comparison line (one CTA applying d
 # levels): kernel, depth, tile bx x by, z chunk, ring (unused), threads.
 BLOCKED_REF = {"f64": (4, 4, 64, 32, 64, 0, 512), "f32": (4, 4, 32, 32, 128, 0, 256)}  # kernel TB_CTA
-# DRAM bytes per LUP of one launch, from the ncu captures summarised under
-# profiles/ (same kernel build): (kernel, dtype, depth) -> (bytes per LUP,
-# summary).
-BATCH_SWEEP_TRAFFIC = (12.62, "profiles/batch_sweep_256grids.md (DRAM bytes per LUP, one sweep of the batch)")
+# DRAM bytes per LUP of one launch (dram__bytes_read.sum + dram__bytes_write.sum
+# over the LUPs of the launch), from ncu captures of the same kernel build:
+# (kernel, dtype, depth) -> (bytes per LUP, capture tag).
+BATCH_SWEEP_TRAFFIC = (12.62, "ncu: batch_sweep_kernel, 256-grid workload, one sweep")
 MEASURED_TRAFFIC = {
-    ("plain_pass_kernel", "f64", 1): (15.92, "profiles/plain_pass_fp64_512cubed.md"),
-    ("tbc4_pass_kernel", "f32", 2): (3.97, "profiles/tbc4_pass_fp32_d2_512cubed.md"),
-    ("tbc4_pass_kernel", "f32", 4): (2.04, "profiles/tbc4_pass_fp32_d4_512cubed.md"),
+    ("plain_pass_kernel", "f64", 1): (15.92, "ncu: plain_pass_kernel<double>, 512^3"),
+    ("tbc4_pass_kernel", "f32", 2): (3.97, "ncu: tbc4_pass_kernel depth 2, FP32 512^3"),
+    ("tbc4_pass_kernel", "f32", 4): (2.04, "ncu: tbc4_pass_kernel depth 4, FP32 512^3"),
 }
 SM_MAX_MHZ = 2070.0
 
@@ -201,47 +202,155 @@ def cpu_oracle_sample(w, budget_s: float):
             "single_thread": {"value": g1, "unit": "GLUP/s", "sample": "2 sweeps of the same grid on 1 core"}}
 
 
+# ------------------------------------------------------------------ context
+class Ctx:
+    """Process placement: rank, world size, local GPU, and the process group
+    (None for a single process)."""
+
+    def __init__(self, gpu: bool):
+        self.dist, self.rank, self.ws, self.local = _dist()
+        self.dev = None
+        if gpu:
+            import torch
+            if self.dist is not None:
+                torch.cuda.set_device(self.local)
+                self.dist.init_process_group("nccl")
+            self.dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier(self):
+        import torch
+        torch.cuda.synchronize()
+        if self.dist is not None:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+
+    def close(self):
+        if self.dist is not None and self.dev is not None:
+            self.dist.barrier()
+            self.dist.destroy_process_group()
+
+
+def _parallelism(ws: int) -> str:
+    return "replicas" if ws > 1 else "single"
+
+
+def grid_config(w, ws: int) -> dict:
+    """The workload's config keys, identical in both arms."""
+    nx, ny, nz = w["n"]
+    es = 8 if w["dtype"] == "f64" else 4
+    return {"workload": w["name"], "nx": nx, "ny": ny, "nz": nz, "T": w["T"], "parallelism": _parallelism(ws),
+            "l2": "inputs larger than L2 (two %.2f GB grids)" % ((nx + 2) * (ny + 2) * (nz + 2) * es / 1e9)}
+
+
+def batch_config(w, ws: int) -> dict:
+    from paper_1006_3148_gb300 import inputs
+    dims, f32 = inputs.batch_dims(256, seed=w["seed"])
+    nbytes = sum((nx + 2) * (ny + 2) * (nz + 2) * (4 if f else 8) for (nx, ny, nz), f in zip(dims, f32))
+    return {"workload": w["name"], "grids": len(dims), "T": w["T"], "fp32_grids": int(sum(f32)),
+            "cells": int(sum(nx * ny * nz for nx, ny, nz in dims)), "parallelism": _parallelism(ws),
+            "l2": "inputs larger than L2 (%.2f GB of grids)" % (2 * nbytes / 1e9)}
+
+
+def poisson_config(w, ws: int) -> dict:
+    return {"workload": w["name"], "nx": w["n"][0], "ny": w["n"][1], "nz": w["n"][2], "inner_sweeps": w["T"],
+            "tol": 1e-10, "parallelism": _parallelism(ws)}
+
+
+def _ref_line(args, w, value, unit, hib, ms_per_step, dtype, config, cores, sample):
+    return {
+        "impl": "reference", "metric": METRIC if unit == "GLUP/s" else POISSON_METRIC, "value": value, "unit": unit,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": hib, "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
 def run_reference(args, w):
-    dist, rank, ws, _ = _dist()
-    if rank != 0:
-        return 0
+    """The CPU oracle as it stands, timed on the host cores on a bounded
+    sample of the workload per step; rank 0 only."""
+    ctx = Ctx(gpu=False)
+    if ctx.rank != 0:
+        return None
     import numpy as np
     import oracle
+    from paper_1006_3148_gb300 import inputs
 
-    nx, ny, nz = w["n"]
-    A = _make_grid(w, "cpu").numpy()
-    B = np.empty_like(A)
-    per_step = 2  # bounded sample per step: 2 sweeps of the full grid
-    for _ in range(args.warmup):
-        oracle.jacobi(A, B, per_step)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.jacobi(A, B, per_step)
-    dt = time.perf_counter() - t0
-    g = nx * ny * nz * per_step * args.steps / dt / 1e9
-    line = {
-        "impl": "reference", "metric": METRIC, "value": g, "unit": "GLUP/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": w["dtype"],
-        "data": "synthetic", "config": {"workload": w["name"], "nx": nx, "ny": ny, "nz": nz, "T": w["T"],
-                                        "sample": "%d sweeps per step" % per_step},
-        "cpu_baseline": {"value": g, "unit": "GLUP/s", "cores": oracle.threads(), "kind": "oracle",
-                         "sample": "%d sweeps per step of the %dx%dx%d grid" % (per_step, nx, ny, nz)},
-        "e2e": {"value": g, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
-    return 0
+    cores = oracle.threads()
+    if w["gen"] == "batch":
+        # per step: the next 4 grids of the batch, T sweeps each
+        dims, f32 = inputs.batch_dims(256, seed=w["seed"])
+        grids = [(g, inputs.uniform_grid(*d, seed=1000 + g).to(
+            __import__("torch").float32 if f32[g] else __import__("torch").float64).numpy())
+            for g, d in enumerate(dims)]
+        per_step = 4
+
+        def step(i):
+            lups = 0
+            for g, a in grids[(per_step * i) % 256:(per_step * i) % 256 + per_step]:
+                oracle.jacobi(a.copy(), np.empty_like(a), w["T"])
+                lups += a[1:-1, 1:-1, 1:-1].size * w["T"]
+            return lups
+        for i in range(args.warmup):
+            step(i)
+        t0, lups = time.perf_counter(), 0
+        for i in range(args.steps):
+            lups += step(args.warmup + i)
+        dt = time.perf_counter() - t0
+        g = lups / dt / 1e9
+        line = _ref_line(args, w, g, "GLUP/s", True, dt * 1e3 / args.steps, "f64+f32", batch_config(w, ctx.ws),
+                         cores, "%d grids of the batch per step (next in order), %d sweeps each" % (per_step, w["T"]))
+    elif w["gen"] == "poisson":
+        # one full refinement solve gives the outer-step count; each timed
+        # step is one outer step (residual + inner sweeps + update); the
+        # value is the time per outer step x the outer steps of the solve
+        n = w["n"][0]
+        hg = 1.0 / (n + 1)
+        f = inputs.normal_rhs(n, n, n, seed=w["seed"]).numpy()
+        u = np.zeros_like(f)
+        st, outer_full, rel = oracle.refine(u, f, hg, 1e-10, w["T"], 400)
+        u = np.zeros_like(f)
+        for _ in range(args.warmup):
+            oracle.refine(u, f, hg, 0.0, w["T"], 1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle.refine(u, f, hg, 0.0, w["T"], 1)
+        per_outer = (time.perf_counter() - t0) / args.steps
+        value = per_outer * outer_full
+        line = _ref_line(args, w, value, "s", False, per_outer * 1e3, "f64+f32", poisson_config(w, ctx.ws), cores,
+                         "one outer refinement step per step (%d inner FP32 sweeps + FP64 residual and update); "
+                         "value = time per outer step x %d outer steps of a full oracle solve" % (w["T"], outer_full))
+    else:
+        nx, ny, nz = w["n"]
+        A = _make_grid(w, "cpu").numpy()
+        B = np.empty_like(A)
+        per_step = 2  # bounded sample per step: 2 sweeps of the full grid
+        for _ in range(args.warmup):
+            oracle.jacobi(A, B, per_step)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle.jacobi(A, B, per_step)
+        dt = time.perf_counter() - t0
+        g = nx * ny * nz * per_step * args.steps / dt / 1e9
+        line = _ref_line(args, w, g, "GLUP/s", True, dt * 1e3 / args.steps, w["dtype"], grid_config(w, ctx.ws), cores,
+                         "%d sweeps per step of the %dx%dx%d grid" % (per_step, nx, ny, nz))
+    return line
 
 
-def run_ours(args, w):
+def _kernel_name(J, kernel: int, dtype: str) -> str:
+    return {J.KERNEL_TB: "tb_pass_kernel", J.KERNEL_PLAIN: "plain_pass_kernel", J.KERNEL_PLAIN_X2: "plain_x2_kernel",
+            J.KERNEL_TB_CTA: "tbc4_pass_kernel" if dtype == "f32" else "tbc_pass_kernel"}[kernel]
+
+
+def run_ours(args, w, ctx, sub=False):
+    """One step = one jacobi_sweep call of T sweeps on the workload's grid.
+    sub: a secondary line inside the default run (no end-to-end, blocked
+    comparison or CPU baseline)."""
     import torch
     from paper_1006_3148_gb300 import jacobi as J
 
-    dist, rank, ws, local = _dist()
-    if dist is not None:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", torch.cuda.current_device())
+    dist, rank, ws, dev = ctx.dist, ctx.rank, ctx.ws, ctx.dev
     nx, ny, nz = w["n"]
     T = w["T"]
     es = 8 if w["dtype"] == "f64" else 4
@@ -252,12 +361,12 @@ def run_ours(args, w):
     A = _make_grid(w, dev)
     B = torch.empty_like(A)
     tune_glups = None
-    if args.plan:
+    if args.plan and not sub:
         f = args.plan.split(":")
         ring = int(f[5]) if len(f) > 5 else 0
         threads = int(f[6]) if len(f) > 6 else 0
-        J.jacobi_set_plan(h, {"tb": J.KERNEL_TB, "plain": J.KERNEL_PLAIN, "x2": J.KERNEL_PLAIN_X2, "cta": J.KERNEL_TB_CTA}[f[0]], int(f[1]), int(f[2]), int(f[3]),
-                          int(f[4]), ring, threads)
+        J.jacobi_set_plan(h, {"tb": J.KERNEL_TB, "plain": J.KERNEL_PLAIN, "x2": J.KERNEL_PLAIN_X2,
+                              "cta": J.KERNEL_TB_CTA}[f[0]], int(f[1]), int(f[2]), int(f[3]), int(f[4]), ring, threads)
     elif not args.no_tune:
         sa, sb = torch.empty_like(A), torch.empty_like(A)
         tune_glups = J.jacobi_tune(h, sa, sb)
@@ -266,27 +375,21 @@ def run_ours(args, w):
     plan = J.jacobi_get_plan(h)
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
     J.jacobi_profile_enable(h, True)
     for _ in range(args.warmup):
         J.jacobi_sweep(h, A, B, T, stream)
-    barrier()
+    ctx.barrier()
     J.jacobi_profile_read(h)
-    sampler = ClockSampler(dev.index if dist is None else local)
+    sampler = ClockSampler(dev.index)
     sampler.start()
     time.sleep(0.3)
-    barrier()
+    ctx.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         J.jacobi_sweep(h, A, B, T, stream)
     e1.record(stream)
-    barrier()
+    ctx.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     prof = J.jacobi_profile_read(h)
@@ -319,26 +422,23 @@ def run_ours(args, w):
                             "peak_source": peak_src}}
     if roof is None:
         roof = {"bound": "hbm", "achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
-                "traffic": None, "peak_source": peak_src}
-    roof["kernel"] = {J.KERNEL_TB: "tb_pass_kernel", J.KERNEL_PLAIN: "plain_pass_kernel",
-                      J.KERNEL_PLAIN_X2: "plain_x2_kernel",
-                      J.KERNEL_TB_CTA: "tbc4_pass_kernel" if w["dtype"] == "f32" else "tbc_pass_kernel"}[plan["kernel"]]
+                "traffic": None, "peak_source": peak_src,
+                "note": "algorithmic bytes: read and write the grid once per pass (2 x %d B per cell)" % es}
+    roof["kernel"] = _kernel_name(J, plan["kernel"], w["dtype"])
     roof["avg_launch_ms"] = pass_ms
     roof["sm_mhz_during"] = clk
     measured = MEASURED_TRAFFIC.get((roof["kernel"], w["dtype"], plan["depth"]))
     if measured is not None:
         # bytes per LUP of the captured launch x the LUPs of one launch here
         roof["traffic"] = measured[0] * lup_launch
-        roof["traffic_source"] = measured[1] + " (DRAM bytes per LUP scaled to this launch)"
+        roof["traffic_source"] = measured[1] + " (bytes per LUP x LUPs of this launch)"
 
     p0 = m_s / (2.0 * es)  # Eq. (2) for element size es
     line = {
         "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
-        "config": {"workload": w["name"], "nx": nx, "ny": ny, "nz": nz, "T": T, "plan": plan,
-                   "parallelism": "replicas" if ws > 1 else "single", "l2": "inputs larger than L2 "
-                   "(two %.2f GB grids)" % ((nx + 2) * (ny + 2) * (nz + 2) * es / 1e9)},
+        "config": grid_config(w, ws), "plan": plan,
         "hbm_roofline": {"P0_glups": p0, "per_pass_frac": value / ws / p0,
                          "effective_frac": value / ws / (p0 * plan["depth"]), "M_s_gbs": m_s,
                          "peak_source": peak_src},
@@ -349,7 +449,7 @@ def run_ours(args, w):
     if tune_glups is not None:
         line["tuner_best_glups"] = tune_glups
 
-    # ---- comparison kernels, untimed in value: the scalar single-pass kernel
+    # ---- comparison kernels, outside value: the scalar single-pass kernel
     # (code balance of Eq. (2)) and a temporally blocked pass of fixed depth
     if rank == 0 and not args.no_plain:
         def glups_of(kernel, *fields):
@@ -367,14 +467,15 @@ def run_ours(args, w):
         gp, Tp = glups_of(J.KERNEL_PLAIN)
         line["plain"] = {"value": gp, "unit": "GLUP/s", "sweeps": Tp, "per_pass_frac": gp / p0}
         line["tuned_vs_plain"] = (value / ws) / gp
-        bd = BLOCKED_REF[w["dtype"]]
-        gb, Tb = glups_of(*bd)
-        line["blocked"] = {"value": gb, "unit": "GLUP/s", "sweeps": Tb,
-                           "plan": dict(zip(("kernel", "depth", "bx", "by", "bz", "ring", "threads"), bd)),
-                           "hbm_bytes_per_lup_ideal": 2.0 * es / bd[1]}
+        if not sub:
+            bd = BLOCKED_REF[w["dtype"]]
+            gb, Tb = glups_of(*bd)
+            line["blocked"] = {"value": gb, "unit": "GLUP/s", "sweeps": Tb,
+                               "plan": dict(zip(("kernel", "depth", "bx", "by", "bz", "ring", "threads"), bd)),
+                               "hbm_bytes_per_lup_ideal": 2.0 * es / bd[1]}
 
     # ---- end to end through the host-buffer entry point
-    if not args.no_e2e:
+    if not args.no_e2e and not sub:
         host_in = A.cpu().pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         del A, B
@@ -382,7 +483,7 @@ def run_ours(args, w):
         J.jacobi_profile_enable(h, False)
         for _ in range(2):  # warm-up: device grids of the host entry point, pinned pages
             J.jacobi_sweep_host(h, host_in, host_out, T, stream)
-        barrier()
+        ctx.barrier()
         ke = max(1, min(args.steps, 3))
         calls = []
         t0 = time.perf_counter()
@@ -395,21 +496,20 @@ def run_ours(args, w):
         nbytes = host_in.numel() * es
         line["e2e"] = {"value": ws * lups_step * ke / dt_e / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes, "steps": ke, "call_ms": calls}
+        del host_in, host_out
+    else:
+        del A, B
 
     # ---- CPU oracle baseline on the host cores (rank 0, N = 1 only)
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not sub:
         line["cpu_baseline"] = cpu_oracle_sample(w, args.cpu_budget)
 
     h.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
-    return 0
+    torch.cuda.empty_cache()
+    return line
 
 
-def run_batch(args, w):
+def run_batch(args, w, ctx, sub=False):
     """256 independent grids (sizes U{32..192} per axis, half FP64 / half
     FP32, interior and halo U[0,1), T = 50 each): one step = one
     jacobi_batch_run (a CUDA graph: halo copy, then one launch per sweep over
@@ -419,11 +519,7 @@ def run_batch(args, w):
     from paper_1006_3148_gb300 import inputs
     from paper_1006_3148_gb300 import jacobi as J
 
-    dist, rank, ws, local = _dist()
-    if dist is not None:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", torch.cuda.current_device())
+    dist, rank, ws, dev = ctx.dist, ctx.rank, ctx.ws, ctx.dev
     dims, f32 = inputs.batch_dims(256, seed=w["seed"])
     T = w["T"]
     dts = [torch.float32 if f else torch.float64 for f in f32]
@@ -447,25 +543,19 @@ def run_batch(args, w):
     bytes_alg = float(sum(2 * (4 if f else 8) * nx * ny * nz for (nx, ny, nz), f in zip(dims, f32))) * T
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
     for _ in range(args.warmup):
         J.jacobi_batch_run(b, A, B, stream)
-    barrier()
+    ctx.barrier()
     sampler = ClockSampler(dev.index)
     sampler.start()
     time.sleep(0.3)
-    barrier()
+    ctx.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         J.jacobi_batch_run(b, A, B, stream)
     e1.record(stream)
-    barrier()
+    ctx.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     assert J.jacobi_batch_get_status(b) == 0
@@ -486,7 +576,7 @@ def run_batch(args, w):
         roof = {"bound": "hbm", "achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
                 "traffic": None, "peak_source": peak_src}
     roof["kernel"] = "batch_sweep_kernel" if sweeps_engine else "batch_kernel"
-    if sweeps_engine:
+    if sweeps_engine and BATCH_SWEEP_TRAFFIC is not None:
         # DRAM bytes per LUP of one sweep launch over the batch (ncu capture)
         roof["traffic"] = BATCH_SWEEP_TRAFFIC[0] * lups / T
         roof["traffic_source"] = BATCH_SWEEP_TRAFFIC[1]
@@ -496,23 +586,19 @@ def run_batch(args, w):
         "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": w["name"], "grids": len(dims), "T": T, "fp32_grids": int(sum(f32)),
-                   "cells": int(sum(nx * ny * nz for nx, ny, nz in dims)),
-                   "engine": "sweeps" if sweeps_engine else "persistent",
-                   **({"planes_per_thread": eng["kz"]} if sweeps_engine else
-                      {"tile": [info["bx"], info["by"], info["bz"]], "items": info["items"],
-                       "persistent_ctas": info["blocks"]}),
-                   "parallelism": "replicas" if ws > 1 else "single",
-                   "l2": "inputs larger than L2 (%.2f GB of grids)" % (2 * sum(x.numel() * x.element_size()
-                                                                            for x in A) / 1e9)},
+        "config": batch_config(w, ws),
+        "plan": {"engine": "sweeps" if sweeps_engine else "persistent",
+                 **({"planes_per_thread": eng["kz"]} if sweeps_engine else
+                    {"tile": [info["bx"], info["by"], info["bz"]], "items": info["items"],
+                     "persistent_ctas": info["blocks"]})},
         "roofline": roof, "gpu_launches": launches_per_run * args.steps, "clocks": clocks,
     }
     if tune is not None:
         line["tuner_best_glups"] = tune
-    if not args.no_e2e:
+    if not args.no_e2e and not sub:
         hosts = [x.cpu().pin_memory() for x in A]
         outs_h = [torch.empty_like(x).pin_memory() for x in hosts]
-        barrier()
+        ctx.barrier()
         ke = max(1, min(args.steps, 3))
         t0 = time.perf_counter()
         for _ in range(ke):
@@ -526,7 +612,7 @@ def run_batch(args, w):
         nbytes = sum(x.numel() * x.element_size() for x in hosts)
         line["e2e"] = {"value": ws * lups * ke / dt_e / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes, "steps": ke}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not sub:
         import oracle
         t0 = time.perf_counter()
         done = 0.0
@@ -542,15 +628,12 @@ def run_batch(args, w):
         line["cpu_baseline"] = {"value": done / dt / 1e9, "unit": "GLUP/s", "cores": oracle.threads(),
                                 "kind": "oracle", "sample": "first %d of the 256 grids, %d sweeps each" % (ng, T)}
     b.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
-    return 0
+    del A, B
+    torch.cuda.empty_cache()
+    return line
 
 
-def run_poisson(args, w):
+def run_poisson(args, w, ctx):
     """-Lap u = f, 96^3, h = 1/97, f ~ N(0,1), zero halo: time to a relative
     residual of 1e-10 by mixed-precision refinement (FP64 residual/update,
     500 FP32 inner sweeps per outer step) and by plain FP64 Jacobi.  One
@@ -561,7 +644,7 @@ def run_poisson(args, w):
 
     n = w["n"][0]
     hg = 1.0 / (n + 1)
-    f = inputs.normal_rhs(n, n, n, seed=w["seed"]).cuda()
+    f = inputs.normal_rhs(n, n, n, seed=w["seed"]).to(ctx.dev)
     H = J.Handle(n, n, n, torch.float64)
     u = torch.zeros_like(f)
     for _ in range(args.warmup):
@@ -594,20 +677,26 @@ def run_poisson(args, w):
             u, tmp = tmp, u
         rel_p = J.jacobi_poisson_residual(H, u, f, hg)
     t_plain = time.perf_counter() - t0
-    line = {
-        "metric": "time to relative residual 1e-10 (Poisson 96^3, refinement vs plain FP64 Jacobi)",
-        "value": t_ref, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_ref * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": w["name"], "inner_sweeps": w["T"], "outer_steps": outers[-1], "final_rel": rel},
+    return {
+        "metric": POISSON_METRIC, "value": t_ref, "unit": "s", "n_gpus": ctx.ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ref * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": poisson_config(w, ctx.ws), "outer_steps": outers[-1], "final_rel": rel,
         "refine_inner_glups": inner_lups / t_ref / 1e9,
         "plain_fp64_jacobi": {"seconds": t_plain, "sweeps": sweeps, "final_rel": rel_p,
                               "glups": float(n ** 3) * sweeps / t_plain / 1e9},
         "speedup_refine_vs_plain_fp64": t_plain / t_ref,
         "gpu_launches": launches,
     }
-    print(json.dumps(line), flush=True)
-    return 0
+
+
+SUB_KEYS = ("value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config", "plan", "hbm_roofline", "roofline",
+            "clocks", "gpu_launches", "tuner_best_glups", "plain", "tuned_vs_plain")
+
+
+def sub_line(line: dict) -> dict:
+    """The keys of a secondary workload's line kept inside the default line."""
+    return {k: line[k] for k in SUB_KEYS if k in line}
 
 
 def main():
@@ -617,11 +706,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fp64_512", choices=sorted(WORKLOADS))
-    ap.add_argument("--plan", default=None, help="force a plan kernel:depth:bx:by:bz[:ring[:threads]], kernel tb, cta, plain or x2, e.g. tb:4:64:16:64:8, cta:4:64:32:64:0:512 or x2:1:32:8:16")
+    ap.add_argument("--plan", default=None, help="force a plan kernel:depth:bx:by:bz[:ring[:threads]], kernel tb, cta, "
+                    "plain or x2, e.g. tb:4:64:16:64:8, cta:4:64:32:64:0:512 or x2:1:32:8:16")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="default workload only: skip the FP32 1024^3 and "
+                    "256-grid batch lines measured beside it")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--n", type=int, default=None, help="override the cubic interior size (profiling cases)")
     ap.add_argument("--T", type=int, default=None, help="override the sweeps per step (profiling cases)")
@@ -629,6 +721,7 @@ def main():
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     w = dict(WORKLOADS[args.workload])
+    resized = args.n is not None or args.T is not None
     if args.n is not None:
         w["n"] = (args.n, args.n, args.n)
         w["name"] += "_resized_%d" % args.n
@@ -636,14 +729,27 @@ def main():
         w["T"] = args.T
         w["name"] += "_T%d" % args.T
     if args.impl == "reference":
-        if w["gen"] in ("batch", "poisson"):
-            return run_reference(args, dict(WORKLOADS["fp64_512"]))
-        return run_reference(args, w)
-    if w["gen"] == "batch":
-        return run_batch(args, w)
-    if w["gen"] == "poisson":
-        return run_poisson(args, w)
-    return run_ours(args, w)
+        line = run_reference(args, w)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return 0
+    ctx = Ctx(gpu=True)
+    try:
+        if w["gen"] == "batch":
+            line = run_batch(args, w, ctx)
+        elif w["gen"] == "poisson":
+            line = run_poisson(args, w, ctx)
+        else:
+            line = run_ours(args, w, ctx)
+            if args.workload == "fp64_512" and not resized and not args.no_sub and not args.plan:
+                # the FP32 and batched workloads, measured in the same run
+                line["fp32_1024"] = sub_line(run_ours(args, dict(WORKLOADS["fp32_1024"]), ctx, sub=True))
+                line["batch256"] = sub_line(run_batch(args, dict(WORKLOADS["batch256"]), ctx, sub=True))
+        if ctx.rank == 0:
+            print(json.dumps(line), flush=True)
+    finally:
+        ctx.close()
+    return 0
 
 
 if __name__ == "__main__":

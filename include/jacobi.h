@@ -150,6 +150,16 @@ int jacobi_get_plan(jacobi_h h, int *kernel, int *depth, int *bx, int *by, int *
 int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stream,
                 double *glups);
 
+/* The autotuner's first-stage candidate plans for this handle (the plans
+ * jacobi_tune times before refining the winner), restricted to those this
+ * device can launch: writes up to max_plans plans as 7 ints each (kernel,
+ * depth, bx, by, bz, ring, threads, the fields of jacobi_set_plan) to
+ * plans[0 .. 7*max_plans-1] and returns the total number of candidates
+ * (which may exceed max_plans), or a negative JACOBI_ERR_* code.  No device
+ * work beyond occupancy queries.  Serves tests that force every plan the
+ * tuner can choose (Sect. 2.4's parameter sweeps). */
+int jacobi_tune_candidates(jacobi_h h, int *plans, int max_plans);
+
 /* Pass planning (host only, no device work): splits T >= 0 sweeps into
  * passes of depth <= depth (>= 1) whose count has the parity of T, as even
  * as possible (a team sweep of Sect. 2.1 applies t*T updates; here a pass
@@ -214,8 +224,9 @@ int jacobi_poisson_residual(jacobi_h h, const void *u, const void *f, double hgr
 
 /* Plain FP64 Jacobi for the Poisson problem: `sweeps` sweeps of
  * u <- (neighbour sum + h^2 f)/6 (order of Eq. 1, h^2 f added last, IEEE
- * division), u and tmp in turn, all in one persistent launch; result in tmp
- * if sweeps is odd, else in u (tmp's halo is set from u's).  Asynchronous. */
+ * division), u and tmp in turn: one single-pass sweep kernel per sweep,
+ * replayed from a CUDA graph cached on the handle; result in tmp if sweeps
+ * is odd, else in u (tmp's halo is set from u's).  Asynchronous. */
 int jacobi_poisson_jacobi(jacobi_h h, void *u, void *tmp, const void *f, double hgrid, int sweeps,
                           jacobi_stream_t stream);
 
@@ -223,7 +234,8 @@ int jacobi_poisson_jacobi(jacobi_h h, void *u, void *tmp, const void *f, double 
  *   loop: r = f - A_h u in FP64, rel = ||r||/||f||; stop if rel <= rel_tol
  *         or max_outer corrections were applied; g = RN_f32(h^2 r);
  *         e = 0 and inner_sweeps FP32 Jacobi sweeps e <- (sum(e) + g)/6 on
- *         A_h e = r (zero halo, one persistent launch); u += (double)e.
+ *         A_h e = r (zero halo; single-pass sweep kernels replayed from
+ *         a CUDA graph cached on the handle); u += (double)e.
  * Only the residual and the update run in FP64.  *outer_done = corrections
  * applied, *final_rel_residual = last rel (both may be NULL).  Returns
  * JACOBI_ERR_NOT_CONVERGED if rel_tol was not reached.  Synchronises stream
@@ -249,9 +261,9 @@ int jacobi_refine(jacobi_h h, double *u, const double *f, double hgrid, double r
  * Its scratch is a fixed device array inside the library (size: see
  * JACOBI_NOALLOC_MAX_NZ); nz > JACOBI_NOALLOC_MAX_NZ returns JACOBI_ERR_ARG.
  * u, f: device grids of interior nx*ny*nz as in jacobi_create; the result
- * is read back, so the call synchronises stream.  The first call on a
- * device looks up the array's device address (once per device, with that
- * device current); make that first call before any stream capture.  All
+ * is read back, so the call synchronises stream.  Every call looks up the
+ * array's device address in the current device's context (a lookup, not an
+ * allocation), so the address is never stale after a context reset.  All
  * calls share the one array: calls that overlap on the GPU (several streams
  * or threads at once) race and must be serialised by the caller. */
 int jacobi_poisson_residual_noalloc(const void *u, const void *f, int nx, int ny, int nz,

@@ -37,24 +37,28 @@ size_t grid_elems(const jacobi_plan_s *h)
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, Plan> g_tune_cache;
 
+// Plan of a handle that was neither tuned nor forced: the kernel families the
+// tuner measured fastest on this GPU at large sizes.  FP64: the single-pass
+// kernel (the FP64 sweep is bound by the FP64 pipe, so temporal blocking
+// only adds redundant work); FP32: temporal blocking inside one CTA at
+// depth 2.  Tiles are clamped to the grid.
 Plan default_plan(const jacobi_plan_s *h)
 {
     Plan p;
-    p.kernel = JACOBI_KERNEL_TB;
     if (h->dtype == JACOBI_F64) {
+        p.kernel = JACOBI_KERNEL_PLAIN;
         p.depth = 1;
         p.bx = 64;
-        p.by = 16;
-        p.bz = 64;
-    } else {
-        p.depth = 4;
-        p.bx = 64;
-        p.by = 32;
-        p.bz = 128;
+        p.by = 4;
+        p.bz = 4;
+        return p;
     }
-    if (p.bx > h->nx) p.bx = h->nx;
-    if (p.by > h->ny) p.by = h->ny;
-    if (p.bz > h->nz) p.bz = h->nz;
+    p.kernel = JACOBI_KERNEL_TB_CTA;
+    p.depth = 2;
+    p.bx = std::min(64, h->nx);
+    p.by = std::min(24, h->ny);
+    p.bz = std::min(128, h->nz);
+    p.threads = 256;
     return p;
 }
 
@@ -458,6 +462,69 @@ int time_plan(jacobi_plan_s *h, const Plan &p, void *A, void *B, cudaStream_t s,
     return JACOBI_OK;
 }
 
+Plan clamp_tile(const jacobi_plan_s *h, Plan p)
+{
+    if (p.bx > h->nx) p.bx = h->nx;
+    if (p.by > h->ny) p.by = h->ny;
+    if (p.bz > h->nz) p.bz = h->nz;
+    return p;
+}
+
+// Stage-1 candidates of the autotuner (Sect. 2.4's parameter sweeps): the
+// single-pass kernels over CTA shapes x planes per thread, temporal
+// blocking inside one CTA over depth x tile x CTA width x z chunk, and the
+// cluster pipeline over depth x tile.  Tiles are clamped to the grid;
+// candidates the device cannot launch are filtered by the caller.
+std::vector<Plan> tune_candidates(const jacobi_plan_s *h)
+{
+    std::vector<Plan> out;
+    const bool f64 = h->dtype == JACOBI_F64;
+    const int plain_shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {32, 16}, {64, 8}, {128, 4}, {256, 2}, {64, 16}};
+    const int plain_kz[] = {4, 8, 16, 32};
+    for (int kern : {JACOBI_KERNEL_PLAIN, JACOBI_KERNEL_PLAIN_X2})
+        for (const auto &b : plain_shapes)
+            for (int kz : plain_kz) {
+                Plan p;
+                p.kernel = kern;
+                p.depth = 1;
+                p.bx = b[0];
+                p.by = b[1];
+                p.bz = kz;
+                out.push_back(p);
+            }
+    const int cta_tiles[][2] = {{32, 32}, {64, 24}, {64, 32}, {128, 16}};
+    for (int d = 1; d <= 4; ++d)
+        for (const auto &t : cta_tiles)
+            for (int nt : {256, 512})
+                for (int bz : {64, 128}) {
+                    Plan p;
+                    p.kernel = JACOBI_KERNEL_TB_CTA;
+                    p.depth = d;
+                    p.bx = t[0];
+                    p.by = t[1];
+                    p.bz = bz;
+                    p.threads = nt;
+                    out.push_back(clamp_tile(h, p));
+                }
+    const int depths64[] = {1, 2, 4};
+    const int depths32[] = {1, 2, 4, 6, 8};
+    const int tiles[][2] = {{32, 16}, {64, 8}, {64, 16}, {32, 32}, {64, 32}, {128, 16}, {128, 32}, {64, 64}};
+    const int *dl = f64 ? depths64 : depths32;
+    const int nd = f64 ? 3 : 5;
+    for (int di = 0; di < nd; ++di)
+        for (const auto &t : tiles) {
+            Plan p;
+            p.kernel = JACOBI_KERNEL_TB;
+            p.depth = dl[di];
+            p.bx = t[0];
+            p.by = t[1];
+            p.bz = 128;
+            p.ring = 0;
+            out.push_back(clamp_tile(h, p));
+        }
+    return out;
+}
+
 }  // namespace
 
 extern "C" {
@@ -467,21 +534,9 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
     if (!h || !scratchA || !scratchB || scratchA == scratchB) return JACOBI_ERR_ARG;
     if (!aligned16(scratchA) || !aligned16(scratchB)) return JACOBI_ERR_ALIGN;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool f64 = h->dtype == JACOBI_F64;
-    // Stage 1: depth x tile with the automatic ring depth and a fixed z chunk.
-    // Stage 2: z chunk and ring depth (pipeline looseness) around the winner.
-    const int depths64[] = {1, 2, 4};
-    const int depths32[] = {1, 2, 4, 6, 8};
-    const int tiles[][2] = {{32, 16}, {64, 8}, {64, 16}, {32, 32}, {64, 32}, {128, 16}, {128, 32}, {64, 64}};
     const int bzs[] = {32, 64, 128, 256};
     const int rings[] = {4, 8, 16};
     const int widths[] = {0, 128, 256, 512};
-    auto clampp = [&](Plan p) {
-        if (p.bx > h->nx) p.bx = h->nx;
-        if (p.by > h->ny) p.by = h->ny;
-        if (p.bz > h->nz) p.bz = h->nz;
-        return p;
-    };
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -511,47 +566,10 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
             bestp = p;
         }
     };
-    const int *dl = f64 ? depths64 : depths32;
-    const int nd = f64 ? 3 : 5;
-    // The single-pass kernel competes too: CTA shapes x planes per thread.
-    const int plain_shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {32, 16}, {64, 8}, {128, 4}, {256, 2}, {64, 16}};
-    const int plain_kz[] = {4, 8, 16, 32};
-    for (int kern : {JACOBI_KERNEL_PLAIN, JACOBI_KERNEL_PLAIN_X2})
-        for (const auto &b : plain_shapes)
-            for (int kz : plain_kz) {
-                Plan p;
-                p.kernel = kern;
-                p.depth = 1;
-                p.bx = b[0];
-                p.by = b[1];
-                p.bz = kz;
-                consider(p);
-            }
-    // Temporal blocking inside one CTA: depth x tile x CTA width x z chunk.
-    const int cta_tiles[][2] = {{32, 32}, {64, 24}, {64, 32}, {128, 16}};
-    for (int d = 1; d <= 4; ++d)
-        for (const auto &t : cta_tiles)
-            for (int nt : {256, 512})
-                for (int bz : {64, 128}) {
-                    Plan p;
-                    p.kernel = JACOBI_KERNEL_TB_CTA;
-                    p.depth = d;
-                    p.bx = t[0];
-                    p.by = t[1];
-                    p.bz = bz;
-                    p.threads = nt;
-                    consider(clampp(p));
-                }
-    for (int di = 0; di < nd; ++di)
-        for (const auto &t : tiles) {
-            Plan p;
-            p.depth = dl[di];
-            p.bx = t[0];
-            p.by = t[1];
-            p.bz = 128;
-            p.ring = 0;
-            consider(clampp(p));
-        }
+    // Stage 1: every family over its shapes and depths.
+    for (const Plan &p : tune_candidates(h)) consider(p);
+    // Stage 2 (cluster pipeline only): z chunk, ring depth (pipeline
+    // looseness) and CTA width around the winner.
     if (st == JACOBI_OK && best > 0 && bestp.kernel == JACOBI_KERNEL_TB) {
         const Plan base = bestp;
         for (int bz : bzs)
@@ -559,13 +577,13 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
                 Plan p = base;
                 p.bz = bz;
                 p.ring = rg;
-                consider(clampp(p));
+                consider(clamp_tile(h, p));
             }
         const Plan base2 = bestp;
         for (int w : widths) {
             Plan p = base2;
             p.threads = w;
-            consider(clampp(p));
+            consider(clamp_tile(h, p));
         }
     }
     cudaEventDestroy(e0);
@@ -579,6 +597,26 @@ int jacobi_tune(jacobi_h h, void *scratchA, void *scratchB, jacobi_stream_t stre
     h->forced = false;
     if (glups) *glups = best;
     return JACOBI_OK;
+}
+
+int jacobi_tune_candidates(jacobi_h h, int *plans, int max_plans)
+{
+    if (!h || max_plans < 0 || (max_plans > 0 && !plans)) return JACOBI_ERR_ARG;
+    std::vector<Plan> c;
+    for (const Plan &p : tune_candidates(h))
+        if (check_plan(h, p) == JACOBI_OK) c.push_back(p);
+    const int n = (int)std::min<size_t>(c.size(), (size_t)max_plans);
+    for (int i = 0; i < n; ++i) {
+        int *o = plans + 7 * i;
+        o[0] = c[i].kernel;
+        o[1] = c[i].depth;
+        o[2] = c[i].bx;
+        o[3] = c[i].by;
+        o[4] = c[i].bz;
+        o[5] = c[i].ring;
+        o[6] = c[i].threads;
+    }
+    return (int)c.size();
 }
 
 }  // extern "C"

@@ -42,8 +42,8 @@ __device__ __forceinline__ double div6_rn(double s)
 __device__ __forceinline__ double add_rn(double x, double y) { return __dadd_rn(x, y); }
 
 // x + y in binary64, round to nearest even, computed on the integer pipe
-// (the FP64 pipe of this GPU retires only ~1.6 additions per SM per clock,
-// so part of the additions of a sweep run here instead).  Fast path: both
+// (the FP64 pipe of this GPU retires at most 2 additions per SM per clock,
+// so part of the additions of a sweep can run here instead).  Fast path: both
 // operands finite and normal with biased exponent <= 2045, same sign; the
 // magnitudes are added (no cancellation) and rounded once:
 //   with |a| >= |b|, d = e_a - e_b: if d >= 54 then |b| < ulp(a)/2 and the

@@ -9,7 +9,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "jacobi_internal.h"
 
@@ -24,10 +23,6 @@ constexpr int kThreads = 256;
 // Every element a call reads was written earlier in the same call, so
 // nothing needs clearing between calls.
 __device__ __align__(256) double g_noalloc_scratch[2 * kMaxPlanes + 2];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double *g_scratch_ptr[kMaxDevices] = {};
 
 __device__ __forceinline__ double block_sum(double v)
 {
@@ -82,20 +77,16 @@ __global__ void totals_kernel(int nz, double *scratch)
     }
 }
 
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current).
+// Device address of the scratch array in the current device's context.  It is
+// looked up on every call (no allocation, a table lookup in the runtime):
+// an address kept from an earlier call would go stale if the context were
+// reset and the module loaded again.
 int scratch_address(double **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return JACOBI_ERR_CUDA;
-    if (dev < 0 || dev >= kMaxDevices) return JACOBI_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        double *p = nullptr;
-        if (cudaGetSymbolAddress((void **)&p, g_noalloc_scratch) != cudaSuccess) return JACOBI_ERR_CUDA;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    double *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return JACOBI_ERR_CUDA;
+    *out = p;
     return JACOBI_OK;
 }
 
@@ -112,11 +103,21 @@ extern "C" int jacobi_poisson_residual_noalloc(const void *u, const void *f, int
     if (st != JACOBI_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const double h2 = hgrid * hgrid;
-    jac::plane_sums_kernel<<<nz, jac::kThreads, 0, s>>>(static_cast<const double *>(u),
-                                                         static_cast<const double *>(f), nx, ny, 1.0 / h2, scratch);
-    jac::totals_kernel<<<1, 32, 0, s>>>(nz, scratch);
+    const double *pu = static_cast<const double *>(u), *pf = static_cast<const double *>(f);
+    const double inv_h2 = 1.0 / h2;
+    // Launched through cudaLaunchKernelEx so that each launch's own status is
+    // checked (cudaGetLastError could report an unrelated earlier error).
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nz);
+    cfg.blockDim = dim3(jac::kThreads);
+    cfg.stream = s;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, jac::plane_sums_kernel, pu, pf, nx, ny, inv_h2, scratch);
+    if (e == cudaSuccess) {
+        cfg.gridDim = dim3(1);
+        cfg.blockDim = dim3(32);
+        e = cudaLaunchKernelEx(&cfg, jac::totals_kernel, nz, scratch);
+    }
     double tot[2] = {0.0, 0.0};
-    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(tot, scratch + 2 * jac::kMaxPlanes, sizeof(tot), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -1,5 +1,5 @@
 // Thin inline-PTX wrappers for sm_103a: mbarriers, cluster/DSMEM access,
-// bulk async copies (TMA engine) and timers.  Every wait loop built on these
+// asynchronous copies and timers.  Every wait loop built on these
 // is bounded by a time limit (see wait_parity_bounded).
 #pragma once
 #include <cstdint>
@@ -28,11 +28,6 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
 __device__ __forceinline__ void cluster_sync_all()
 {
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
-}
-
-__device__ __forceinline__ void named_bar_sync(int id, int nthreads)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 // ---------------------------------------------------------------- mbarrier
@@ -79,12 +74,6 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
 // ----------------------------------------------------------- cluster / DSMEM
 // Address of the same shared-memory location in CTA `rank` of this cluster.
 __device__ __forceinline__ uint32_t mapa(uint32_t local, uint32_t rank)
@@ -92,28 +81,6 @@ __device__ __forceinline__ uint32_t mapa(uint32_t local, uint32_t rank)
     uint32_t r;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
     return r;
-}
-
-__device__ __forceinline__ void st_cluster(uint32_t addr, double v)
-{
-    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
-}
-__device__ __forceinline__ void st_cluster(uint32_t addr, float v)
-{
-    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
-}
-
-// 16-byte store of a group to another CTA's shared memory.  No "memory"
-// clobber: ordering against the consumer is established by the barrier and
-// the release-arrive that follow, which are themselves ordered asm.
-__device__ __forceinline__ void st_cluster_v(uint32_t addr, const float (&v)[4])
-{
-    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v[0]), "f"(v[1]), "f"(v[2]),
-                 "f"(v[3]));
-}
-__device__ __forceinline__ void st_cluster_v(uint32_t addr, const double (&v)[2])
-{
-    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(addr), "d"(v[0]), "d"(v[1]));
 }
 
 // Asynchronous 16-byte store into another CTA's shared memory whose byte
@@ -138,22 +105,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
         "{\n\t.reg .b64 st;\n\t"
         "mbarrier.arrive.expect_tx.relaxed.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
         "r"(bytes)
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_acq_rel_cluster()
-{
-    asm volatile("fence.acq_rel.cluster;" ::: "memory");
-}
-
-// ------------------------------------------------------------ bulk copies
-// Global -> this CTA's shared memory, completion counted in bytes on `bar`.
-// dst, src 16-byte aligned; bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
 

@@ -67,6 +67,7 @@ def load(build_if_missing: bool = True):
             "jacobi_set_plan": ([P, i, i, i, i, i, i, i], i),
             "jacobi_get_plan": ([P, pi, pi, pi, pi, pi, pi, pi], i),
             "jacobi_tune": ([P, P, P, P, ctypes.POINTER(d)], i),
+            "jacobi_tune_candidates": ([P, pi, i], i),
             "jacobi_get_status": ([P, pi], i),
             "jacobi_debug_set_fault": ([P, i, i], i),
             "jacobi_plan_passes": ([i, i, pi, i], i),
@@ -203,6 +204,20 @@ def jacobi_tune(h: Handle, scratchA: torch.Tensor, scratchB: torch.Tensor, strea
     _check(load().jacobi_tune(h.ptr, _grid_ptr(scratchA, h.shape, h.dtype), _grid_ptr(scratchB, h.shape, h.dtype),
                               _stream(stream), ctypes.byref(g)), "jacobi_tune")
     return g.value
+
+
+def jacobi_tune_candidates(h: Handle) -> list:
+    """The tuner's first-stage candidate plans that this device can launch,
+    as tuples (kernel, depth, bx, by, bz, ring, threads)."""
+    L = load()
+    n = L.jacobi_tune_candidates(h.ptr, None, 0)
+    if n < 0:
+        raise JacobiError(n, "jacobi_tune_candidates")
+    buf = (ctypes.c_int * (7 * max(n, 1)))()
+    m = L.jacobi_tune_candidates(h.ptr, buf, n)
+    if m < 0:
+        raise JacobiError(m, "jacobi_tune_candidates")
+    return [tuple(buf[7 * k:7 * k + 7]) for k in range(min(n, m))]
 
 
 def jacobi_get_status(h: Handle) -> int:

@@ -66,9 +66,14 @@ enum {
     JACOBI_KERNEL_PLAIN_X2 = 3, /* single-pass kernel with two x cells per
                                 thread (vector loads, shuffled x-neighbours,
                                 packed FP32 additions); even nx only          */
-    JACOBI_KERNEL_TB_CTA = 4 /* temporal blocking inside one CTA: depth 1..4
+    JACOBI_KERNEL_TB_CTA = 4, /* temporal blocking inside one CTA: depth 1..4
                                 levels applied to a tile's planes in shared
                                 memory (T updates per thread, Sect. 2.1)     */
+    JACOBI_KERNEL_TB_REG = 5 /* temporal blocking inside one CTA with
+                                register-blocked cells (FP32 only): every
+                                thread keeps a 4 x 4 cell block of each level
+                                in registers and exchanges only its block
+                                boundary through shared memory; depth 1..4  */
 };
 
 typedef struct jacobi_plan_s *jacobi_h;
@@ -121,12 +126,18 @@ int jacobi_sweep_host(jacobi_h h, const void *A_host, void *out_host, int T,
  * (1: one sweep per pass with the input planes staged in shared memory),
  * tile bx*by, z chunk bz, threads 256 or 512 (0 = 512), at most 8 cells
  * (FP64) or 4 quads of 4 cells (FP32) of the widened tile (bx+2d)(by+2d)
- * per thread; ring ignored.  For PLAIN and PLAIN_X2:
+ * per thread; ring ignored.  For TB_REG (FP32 grids only): bx*by is the
+ * region the CTA streams -- the output tile widened by depth cells on each
+ * side -- one of 64x32, 64x64 or 128x32 (threads = bx*by/16, each owning
+ * 4 x 4 cells), depth 1..4, z chunk bz; the output tile is (bx - 2 depth,
+ * rounded down to even when nx is even) x (by - 2 depth); ring and threads
+ * ignored.  For PLAIN and PLAIN_X2:
  * bx*by = CTA shape in threads (bx a multiple of 32, bx*by <= 1024; a
  * PLAIN_X2 thread covers two x cells) and bz = planes each thread walks in
  * z; ring and threads are ignored.  A zero bx, by or bz takes the family's
  * default (PLAIN 32 x 8 x 8; PLAIN_X2 32 x 8 x 16; TB 64 x 16 x 64; TB_CTA
- * 64 x 32 x 64; tiles clamped to the grid).  JACOBI_KERNEL_AUTO returns to
+ * 64 x 32 x 64; TB_REG region 64 x 32, 64 planes; tiles clamped to the
+ * grid).  JACOBI_KERNEL_AUTO returns to
  * the tuned/default plan.  Returns JACOBI_ERR_ARG for out-of-range fields and JACOBI_ERR_UNSUPPORTED
  * if the plan cannot launch on this device (shared memory, registers,
  * cluster occupancy). */

@@ -40,8 +40,8 @@ std::map<std::tuple<int, int, int, int, int>, Plan> g_tune_cache;
 // Plan of a handle that was neither tuned nor forced: the kernel families the
 // tuner measured fastest on this GPU at large sizes.  FP64: the single-pass
 // kernel (the FP64 sweep is bound by the FP64 pipe, so temporal blocking
-// only adds redundant work); FP32: temporal blocking inside one CTA at
-// depth 2.  Tiles are clamped to the grid.
+// only adds redundant work); FP32: the register-blocked one-CTA kernel at
+// depth 3 on 64 x 32 regions.  z chunks are clamped to the grid.
 Plan default_plan(const jacobi_plan_s *h)
 {
     Plan p;
@@ -53,12 +53,12 @@ Plan default_plan(const jacobi_plan_s *h)
         p.bz = 4;
         return p;
     }
-    p.kernel = JACOBI_KERNEL_TB_CTA;
-    p.depth = 2;
-    p.bx = std::min(64, h->nx);
-    p.by = std::min(24, h->ny);
+    p.kernel = JACOBI_KERNEL_TB_REG;
+    p.depth = 3;
+    p.bx = 64;
+    p.by = 32;
     p.bz = std::min(128, h->nz);
-    p.threads = 256;
+    p.threads = 128;
     return p;
 }
 
@@ -94,6 +94,14 @@ bool prof_event(jacobi_plan_s *h, cudaStream_t s)
 Plan resolve_plan(const jacobi_plan_s *h, Plan p)
 {
     const bool plain = p.kernel == JACOBI_KERNEL_PLAIN || p.kernel == JACOBI_KERNEL_PLAIN_X2;
+    if (p.kernel == JACOBI_KERNEL_TB_REG) {
+        if (p.bx == 0) p.bx = 64;
+        if (p.by == 0) p.by = 32;
+        if (p.bz == 0) p.bz = std::min(64, h->nz);
+        p.ring = 0;
+        p.threads = p.bx * p.by / 16;
+        return p;
+    }
     if (p.bx == 0) p.bx = plain ? 32 : std::min(64, h->nx);
     if (p.by == 0) p.by = plain ? 8 : std::min(p.kernel == JACOBI_KERNEL_TB_CTA ? 32 : 16, h->ny);
     if (p.bz == 0) p.bz = plain ? (p.kernel == JACOBI_KERNEL_PLAIN_X2 ? 16 : 8) : std::min(64, h->nz);
@@ -111,6 +119,18 @@ int check_plan(const jacobi_plan_s *h, const Plan &p)
         // (row block, z chunk) pairs must fit grid y * grid z
         const long long pairs = (long long)((h->ny + p.by - 1) / p.by) * ((h->nz + p.bz - 1) / p.bz);
         return pairs <= 65535ll * 65535ll ? JACOBI_OK : JACOBI_ERR_UNSUPPORTED;
+    }
+    if (p.kernel == JACOBI_KERNEL_TB_REG) {
+        if (p.depth < 1 || p.depth > 4 || p.bz < 1) return JACOBI_ERR_ARG;
+        TbrArgs a;
+        a.nx = h->nx;
+        a.ny = h->ny;
+        a.nz = h->nz;
+        a.bz = p.bz;
+        size_t smem = 0;
+        const int st = tbr_configure(p.depth, p.bx, p.by, &a, &smem, nullptr);
+        if (st != JACOBI_OK) return st;
+        return h->dtype == JACOBI_F32 ? JACOBI_OK : JACOBI_ERR_UNSUPPORTED;
     }
     if (p.kernel == JACOBI_KERNEL_TB_CTA) {
         if (p.depth < 1 || p.depth > 4 || p.bx < 1 || p.by < 1 || p.bz < 1) return JACOBI_ERR_ARG;
@@ -169,6 +189,23 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
     std::vector<int> depths((size_t)T + 1);
     const int P = plan_passes(T, p.depth, depths.data(), T + 1);
     if (P < 0) return JACOBI_ERR_ARG;
+    if (p.kernel == JACOBI_KERNEL_TB_REG) {
+        TbrArgs a;
+        a.nx = h->nx;
+        a.ny = h->ny;
+        a.nz = h->nz;
+        a.bz = p.bz;
+        for (int q = 0; q < P; ++q) {
+            if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
+            a.src = (q % 2 == 0) ? A : B;
+            a.dst = (q % 2 == 0) ? B : A;
+            e = tbr_launch(depths[q], p.bx, p.by, a, s);
+            if (e != cudaSuccess) return cuda_fail(e);
+            if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
+            if (h->prof) ++h->prof_pass;
+        }
+        return JACOBI_OK;
+    }
     if (p.kernel == JACOBI_KERNEL_TB_CTA) {
         TbcArgs a;
         a.nx = h->nx;
@@ -354,7 +391,7 @@ int jacobi_set_plan(jacobi_h h, int kernel, int depth, int bx, int by, int bz, i
     p.bx = bx;
     p.by = by;
     p.bz = bz;
-    p.ring = (plain || kernel == JACOBI_KERNEL_TB_CTA) ? 0 : ring;
+    p.ring = (plain || kernel == JACOBI_KERNEL_TB_CTA || kernel == JACOBI_KERNEL_TB_REG) ? 0 : ring;
     p.threads = plain ? 0 : threads;
     p = resolve_plan(h, p);
     const int st = check_plan(h, p);
@@ -506,6 +543,22 @@ std::vector<Plan> tune_candidates(const jacobi_plan_s *h)
                     p.threads = nt;
                     out.push_back(clamp_tile(h, p));
                 }
+    if (!f64) {
+        // register-blocked one-CTA kernel: depth x region x z chunk
+        const int regions[][2] = {{64, 32}, {64, 64}, {128, 32}};
+        for (int d = 1; d <= 4; ++d)
+            for (const auto &r : regions)
+                for (int bz : {64, 128}) {
+                    Plan p;
+                    p.kernel = JACOBI_KERNEL_TB_REG;
+                    p.depth = d;
+                    p.bx = r[0];
+                    p.by = r[1];
+                    p.bz = std::min(bz, h->nz);
+                    p.threads = r[0] * r[1] / 16;
+                    out.push_back(p);
+                }
+    }
     const int depths64[] = {1, 2, 4};
     const int depths32[] = {1, 2, 4, 6, 8};
     const int tiles[][2] = {{32, 16}, {64, 8}, {64, 16}, {32, 32}, {64, 32}, {128, 16}, {128, 32}, {64, 64}};

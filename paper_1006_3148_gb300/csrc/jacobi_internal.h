@@ -35,6 +35,19 @@ struct TbcArgs {
     int W, H, WH;    // region: tile widened by the depth on each side
 };
 
+// Arguments of one pass of the register-blocked one-CTA kernel (FP32).
+// Tile t in x covers output columns [1 + t*bx, 1 + (t+1)*bx); its region
+// starts at x_first + t*bx (a multiple of the copy piece A), off cells left
+// of the tile's D-cell margin.
+struct TbrArgs {
+    const void *src;
+    void *dst;
+    int nx, ny, nz;
+    int bx, by, bz;  // output tile (x, y) and z chunk
+    int x_first;     // region origin of tile 0: 1 - D - off
+    int off;         // alignment slack left of the region's margin
+};
+
 struct PlainArgs {
     const void *src;
     void *dst;
@@ -82,6 +95,13 @@ cudaError_t plain_launch(int dtype, PlainArgs a, cudaStream_t s);
 int tbc_configure(int dtype, int depth, int bx, int by, int threads, TbcArgs *a, size_t *smem);
 cudaError_t tbc_launch(int dtype, int depth, int threads, const TbcArgs &a, cudaStream_t s);
 cudaError_t plain_x2_launch(int dtype, PlainArgs a, cudaStream_t s);  // nx even
+// Register-blocked one-CTA temporal blocking (FP32): region W x H (W in
+// {64, 128}, H in {32, 64}; 16 cells per thread), depth 1..4.  Checks the
+// plan and fills the tile fields of a; launches one pass.
+int tbr_configure(int depth, int W, int H, TbrArgs *a, size_t *smem, int *threads);
+cudaError_t tbr_launch(int depth, int W, int H, const TbrArgs &a, cudaStream_t s);
+cudaError_t tbr_launch_a1(int depth, int W, int H, const TbrArgs &a, size_t smem, cudaStream_t s);
+cudaError_t tbr_launch_a2(int depth, int W, int H, const TbrArgs &a, size_t smem, cudaStream_t s);
 cudaError_t fill_launch(int dtype, void *p, long long n, double v, cudaStream_t s);
 cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, int nz, cudaStream_t s);
 

@@ -84,8 +84,9 @@ def _check(shape, seed, dtype, T, plan):
 RAGGED = [(150, 70, 45), (66, 37, 29)]
 
 
-FAMILIES = [J.KERNEL_PLAIN, J.KERNEL_PLAIN_X2, J.KERNEL_TB_CTA, J.KERNEL_TB]
-FAMILY_IDS = ["plain", "x2", "cta", "tb"]
+FAMILIES = [J.KERNEL_PLAIN, J.KERNEL_PLAIN_X2, J.KERNEL_TB_CTA, J.KERNEL_TB, J.KERNEL_TB_REG]
+FAMILY_IDS = ["plain", "x2", "cta", "tb", "reg"]
+FAMILIES64 = FAMILIES[:4]  # the register-blocked family is FP32 only
 
 
 # The candidate lists are read inside the tests (they need the GPU), one
@@ -101,7 +102,7 @@ def test_fp32_every_tuner_candidate_bitwise(family):
                 _check(shape, 21, torch.float32, T, plan)
 
 
-@pytest.mark.parametrize("family", FAMILIES, ids=FAMILY_IDS)
+@pytest.mark.parametrize("family", FAMILIES64, ids=FAMILY_IDS[:4])
 def test_fp64_every_tuner_candidate_bitwise(family):
     plans = [p for p in _candidates(512, torch.float64) if p[0] == family]
     assert plans
@@ -110,6 +111,29 @@ def test_fp64_every_tuner_candidate_bitwise(family):
         for shape in RAGGED:
             for T in sorted({1, d + 1, 2 * d + 1}):
                 _check(shape, 22, torch.float64, T, plan)
+
+
+# odd row pitch (nx odd): the register-blocked kernel copies single cells
+@pytest.mark.parametrize("shape", [(67, 45, 33), (129, 31, 19), (1, 1, 1), (3, 70, 5)])
+def test_fp32_register_blocked_candidates_odd_and_tiny(shape):
+    plans = [p for p in _candidates(1024, torch.float32) if p[0] == J.KERNEL_TB_REG]
+    assert plans
+    for plan in plans:
+        d = plan[1]
+        for T in sorted({1, d + 1, 2 * d + 1}):
+            _check(shape, 24, torch.float32, T, plan)
+
+
+def test_fp64_grids_reject_the_register_blocked_family():
+    h = J.Handle(40, 30, 20, torch.float64)
+    assert J.load().jacobi_set_plan(h.ptr, J.KERNEL_TB_REG, 2, 64, 32, 16, 0, 0) == -9
+    h32 = J.Handle(40, 30, 20, torch.float32)
+    L = J.load()
+    assert L.jacobi_set_plan(h32.ptr, J.KERNEL_TB_REG, 5, 64, 32, 16, 0, 0) == -1
+    assert L.jacobi_set_plan(h32.ptr, J.KERNEL_TB_REG, 2, 96, 32, 16, 0, 0) == -1
+    J.jacobi_set_plan(h32, J.KERNEL_TB_REG, 2)
+    p = J.jacobi_get_plan(h32)
+    assert (p["kernel"], p["bx"], p["by"], p["bz"], p["threads"]) == (J.KERNEL_TB_REG, 64, 32, 20, 128)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
@@ -135,7 +159,8 @@ def test_fp32_mode_workload_256cubed_every_blocked_candidate():
     # of the tuner with its 1024^3 z chunk
     n, T = 256, 200
     A0, e32, e64 = _mode_case(n, T)
-    plans = [None] + [p for p in _candidates(1024, torch.float32) if p[0] == J.KERNEL_TB_CTA and p[4] == 128]
+    plans = [None] + [p for p in _candidates(1024, torch.float32)
+                      if p[0] in (J.KERNEL_TB_CTA, J.KERNEL_TB_REG) and p[4] == 128]
     scale = np.abs(e64).max()
     for plan in plans:
         got = _run((n, n, n), A0, T, plan)

@@ -25,7 +25,7 @@ int tbr_configure(int depth, int W, int H, TbrArgs *a, size_t *smem, int *thread
     if ((a->ny + by - 1) / by > 65535 || (a->nz + a->bz - 1) / a->bz > 65535) return JACOBI_ERR_UNSUPPORTED;
     const int TX = W / 4, TY = H / kTbrVY;
     const size_t lev = (size_t)2 * TY * W + (size_t)2 * TY * TX * kTbrVY;
-    *smem = ((size_t)kTbrR * W * H + 2 * (size_t)depth * lev) * sizeof(float);
+    *smem = ((size_t)tbr_ring(depth) * W * H + 2 * (size_t)depth * lev) * sizeof(float);
     if (*smem > 227 * 1024) return JACOBI_ERR_UNSUPPORTED;
     if (threads) *threads = TX * TY;
     return JACOBI_OK;

@@ -27,6 +27,8 @@
 // tile and no tile needs its neighbours.  Cells on the grid's halo keep
 // their Dirichlet value at every level (they copy the previous level's
 // value through); cells outside the array are never read by exact cells.
+// A CTA whose region lies on the grid's interior in x and y (most of them)
+// runs a copy of the loop without these per-cell cases.
 // In z, a chunk [z0, z1) of output planes starts D planes early and ends
 // D planes late; planes 0 and nz+1 are halo planes and are copied through.
 //
@@ -45,7 +47,11 @@
 namespace jac {
 
 constexpr int kTbrVY = 4;  // rows per thread block
-constexpr int kTbrR = 4;   // input ring slots
+
+// Input ring slots (three planes in flight).  Eight slots at depth >= 3
+// measured slower: the larger shared-memory carve-out leaves less L1 for the
+// copies, which are staged through L1.
+__host__ __device__ constexpr int tbr_ring(int) { return 4; }
 
 // Asynchronous copy of A floats global -> shared; copies src_bytes of them
 // (A*4 or 0) and zero-fills the rest, so the copy needs no branch (a zero
@@ -84,7 +90,7 @@ struct TbrMinBlocks {
 template <int D, int TX, int TY, int A>
 __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr_pass_kernel(const TbrArgs a)
 {
-    constexpr int VY = kTbrVY, R = kTbrR, NT = TX * TY;
+    constexpr int VY = kTbrVY, R = tbr_ring(D), NT = TX * TY;
     constexpr int W = 4 * TX, H = VY * TY;
     constexpr int RING = W * H;                // floats per ring slot
     constexpr int ROWS = 2 * TY * W;           // [top|bottom][ty][x]
@@ -154,18 +160,28 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
     }
     const int cp_off0 = (ya + cp_row) * P + cp_gx;  // plane offset of copy 0 (used only if inside)
     const uint32_t cp_dst0 = smem_addr(ring + cp_row * W + cp_col);
-    auto load_plane = [&](int p) {
+    // FAST: the whole region lies inside the array, so every piece is copied.
+    auto load_plane = [&](int p, auto FAST) {
         if (p >= 0 && p <= a.nz + 1) {
             const float *sp = src + (long long)p * plane;
             const uint32_t d0 = cp_dst0 + (uint32_t)((p & (R - 1)) * RING * 4);
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
-                const bool in = (cp_rows >> j) & 1u;
-                tbr_copy<A>(d0 + (uint32_t)(j * RPJ * W * 4), in ? sp + cp_off0 + j * RPJ * P : sp, in ? 4u * A : 0u);
+                if (decltype(FAST)::value) {
+                    tbr_copy<A>(d0 + (uint32_t)(j * RPJ * W * 4), sp + cp_off0 + j * RPJ * P, 4u * A);
+                } else {
+                    const bool in = (cp_rows >> j) & 1u;
+                    tbr_copy<A>(d0 + (uint32_t)(j * RPJ * W * 4), in ? sp + cp_off0 + j * RPJ * P : sp,
+                                in ? 4u * A : 0u);
+                }
             }
         }
         cp_async_commit();
     };
+    // The region lies on the grid's interior in x and y (every cell of every
+    // thread is updated and copied): the CTA takes the fast path.
+    const bool interior = xa >= 1 && xa + W - 1 <= a.nx && ya >= 1 && ya + H - 1 <= a.ny;
+    const std::false_type slow_c;
     // Rows whose four cells are all stored take two predicated 8-byte
     // stores (A = 2); any other stored cell goes through the scalar path.
     unsigned rowfull = 0;
@@ -200,8 +216,8 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
 
     const int s_begin = z0 - D + 1;
     const int nsteps = z1 - z0 + 2 * D - 2;
-    load_plane(s_begin - 1);
-    load_plane(s_begin);
+    load_plane(s_begin - 1, slow_c);
+    load_plane(s_begin, slow_c);
     cp_async_wait_group<0>();
     __syncthreads();  // every thread's copies of the two planes are complete
     {
@@ -217,11 +233,12 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
     write_bounds(bufs + 1 * D * LEV, q[0][0]);  // plane s_begin, read in step 0 (parity 1)
     __syncthreads();  // ring reads above are performed before their slots are refilled
 #pragma unroll
-    for (int i = 1; i < R; ++i) load_plane(s_begin + i);
+    for (int i = 1; i < R; ++i) load_plane(s_begin + i, slow_c);
 
     const float sixth = 1.0f / 6.0f;
-    auto step = [&](auto J, int t) {
+    auto step = [&](auto J, auto FAST, int t) {
         constexpr int j = decltype(J)::value;
+        constexpr bool fast = decltype(FAST)::value;
         constexpr int iN = (j + 1) % 3, iC = j, iM = (j + 2) % 3;
         const int s = s_begin + t;
         cp_async_wait_group<R - 2>();  // this thread's copies of plane s+1 are complete
@@ -234,18 +251,27 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
                 q[0][iN][r][0] = u.x, q[0][iN][r][1] = u.y, q[0][iN][r][2] = u.z, q[0][iN][r][3] = u.w;
             }
         }
-        load_plane(s + R);  // into the slot of plane s, read in step t-1
         float *wb = bufs + (t & 1) * D * LEV;
         const float *rb = bufs + ((t + 1) & 1) * D * LEV;
+        // neighbour vectors of level l are loaded one level ahead, before
+        // the shared-memory stores of the level in between (the compiler
+        // cannot move loads across stores it cannot prove disjoint)
+        float4 nbv[4];
+        nbv[0] = tbr_ld4(rb + o_above), nbv[1] = tbr_ld4(rb + o_below);
+        nbv[2] = tbr_ld4(rb + o_left), nbv[3] = tbr_ld4(rb + o_right);
+        load_plane(s + R, FAST);  // into the slot of plane s, read in step t-1
         write_bounds(wb, q[0][iN]);
 #pragma unroll
         for (int l = 1; l <= D; ++l) {
             const int k = l - 1;
             const int p = s - l + 1;
             const bool zin = p >= 1 && p <= a.nz;
-            const float *nb = rb + k * LEV;
-            const float4 above = tbr_ld4(nb + o_above), below = tbr_ld4(nb + o_below);
-            const float4 left = tbr_ld4(nb + o_left), right = tbr_ld4(nb + o_right);
+            const float4 above = nbv[0], below = nbv[1], left = nbv[2], right = nbv[3];
+            if (l < D) {
+                const float *nn = rb + l * LEV;
+                nbv[0] = tbr_ld4(nn + o_above), nbv[1] = tbr_ld4(nn + o_below);
+                nbv[2] = tbr_ld4(nn + o_left), nbv[3] = tbr_ld4(nn + o_right);
+            }
             // Cells (0,1) and (2,3) of a row form packed pairs.  The first
             // addition of Eq. (1) (x-neighbours) pairs cells unevenly and is
             // done per cell, straight into a pair; the other four additions
@@ -277,7 +303,14 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
                 hi = __fmul2_rn(hi, six2);
                 v[r][0] = lo.x, v[r][1] = lo.y, v[r][2] = hi.x, v[r][3] = hi.y;
             }
-            if (!(zin && full)) {
+            if (fast) {
+                if (!zin) {  // uniform: a halo plane (or one outside the array)
+#pragma unroll
+                    for (int r = 0; r < VY; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) v[r][c] = q[k][iC][r][c];
+                }
+            } else if (!(zin && full)) {
 #pragma unroll
                 for (int r = 0; r < VY; ++r)
 #pragma unroll
@@ -314,10 +347,19 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
     // Whole rotations of three steps; the up to two extra steps at the end
     // compute planes beyond the chunk (never stored; their loads beyond the
     // array are skipped), so no step needs a guard.
-    for (int t = 0; t < nsteps; t += 3) {
-        step(std::integral_constant<int, 0>(), t);
-        step(std::integral_constant<int, 1>(), t + 1);
-        step(std::integral_constant<int, 2>(), t + 2);
+    if (interior) {
+        const std::true_type f;
+        for (int t = 0; t < nsteps; t += 3) {
+            step(std::integral_constant<int, 0>(), f, t);
+            step(std::integral_constant<int, 1>(), f, t + 1);
+            step(std::integral_constant<int, 2>(), f, t + 2);
+        }
+    } else {
+        for (int t = 0; t < nsteps; t += 3) {
+            step(std::integral_constant<int, 0>(), slow_c, t);
+            step(std::integral_constant<int, 1>(), slow_c, t + 1);
+            step(std::integral_constant<int, 2>(), slow_c, t + 2);
+        }
     }
     cp_async_wait_group<0>();
 }

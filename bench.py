@@ -37,6 +37,18 @@ M_S_FALLBACK = 6800.0  # GB/s, used only if MEASURED_PEAKS.json is absent
 # FP64 pipe of GB300: 1.25 TFLOP/s nominal counting an FMA as 2 flops, i.e.
 # 2 FP64 lanes per SM per clock (1.25e12 / (2 * 152 * 2.07e9)).
 FP64_LANES_PER_SM_CLK = 2
+# Of the five additions of a cell update, the library's FP64 kernels run the
+# first and the last on the integer pipe; three issue on the FP64 pipe.
+FP64_PIPE_ADDS = 3
+# Integer ALU pipe: 16 lanes per SM sub-partition and clock, 64 per SM
+# (ncu: 536.6 M ALU warp instructions in 952.8 us at 90.15 % of peak on the
+# 512^3 launch = 2.0 warp instructions per SM and clock).
+ALU_LANES_PER_SM_CLK = 64
+# ALU-pipe lane instructions per cell update (smsp__inst_executed_pipe_alu.sum
+# x 32 / LUPs of the launch, ncu): kernel, dtype -> (count, capture tag).
+MEASURED_ALU = {
+    ("plain_pass_kernel", "f64"): (128.0, "ncu: plain_pass_kernel<double> 512^3, 32x16 threads, 32 planes"),
+}
 SMS = 152
 # Temporally blocked pass used for the comparison line (one CTA applying d
 # levels): kernel, depth, tile bx x by, z chunk, ring (unused), threads.
@@ -49,6 +61,7 @@ MEASURED_TRAFFIC = {
     ("plain_pass_kernel", "f64", 1): (15.92, "ncu: plain_pass_kernel<double>, 512^3"),
     ("tbc4_pass_kernel", "f32", 2): (3.97, "ncu: tbc4_pass_kernel depth 2, FP32 512^3"),
     ("tbc4_pass_kernel", "f32", 4): (2.04, "ncu: tbc4_pass_kernel depth 4, FP32 512^3"),
+    ("tbr_pass_kernel", "f32", 3): (2.79, "ncu: tbr_pass_kernel depth 3, region 64x32, FP32 512^3, one pass"),
 }
 SM_MAX_MHZ = 2070.0
 
@@ -410,17 +423,27 @@ def run_ours(args, w, ctx, sub=False):
     clk = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
     roof = None
     if w["dtype"] == "f64":
-        # FP64-pipe work per LUP: the 5 additions (the division by 6 runs on
-        # the integer pipe)
-        alu_ach = 5.0 * lup_launch / (pass_ms * 1e-3) / 1e12
-        alu_peak = FP64_LANES_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 1e12
-        if alu_ach / alu_peak > hbm_ach / m_s:
-            roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
+        # FP64 sweeps are bound on chip: three FP64-pipe additions per LUP
+        # (the other two and the division by 6 run on the integer pipe),
+        # whose ALU instructions are the binding unit
+        kname = _kernel_name(J, plan["kernel"], w["dtype"])
+        fp64_ach = FP64_PIPE_ADDS * lup_launch / (pass_ms * 1e-3) / 1e12
+        fp64_peak = FP64_LANES_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 1e12
+        fp64 = {"achieved": fp64_ach, "peak": fp64_peak, "unit": "T adds/s", "frac": fp64_ach / fp64_peak,
+                "note": "FP64 pipe: 2 lanes/SM/clk x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s FMA-counted); "
+                        "%d FP64-pipe additions per LUP" % FP64_PIPE_ADDS}
+        hbm = {"achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s, "peak_source": peak_src}
+        alu = MEASURED_ALU.get((kname, w["dtype"]))
+        if alu is not None:
+            alu_ach = alu[0] * lup_launch / (pass_ms * 1e-3) / 1e12
+            alu_peak = ALU_LANES_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "T int-ops/s",
                     "frac": alu_ach / alu_peak, "traffic": None,
-                    "note": "FP64 pipe: 2 lanes/SM/clk x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s FMA-counted); "
-                            "achieved counts the 5 FP64 additions per LUP (division on the integer pipe)",
-                    "hbm": {"achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
-                            "peak_source": peak_src}}
+                    "note": "integer ALU pipe: 64 lanes/SM/clk x 152 SMs x 2070 MHz; achieved = %.0f ALU lane "
+                            "instructions per LUP (%s) x LUP/s" % alu,
+                    "fp64_pipe": fp64, "hbm": hbm}
+        elif fp64["frac"] > hbm["frac"]:
+            roof = dict(fp64, bound="alu", unit="TFLOP/s", traffic=None, hbm=hbm)
     if roof is None:
         roof = {"bound": "hbm", "achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
                 "traffic": None, "peak_source": peak_src,
@@ -567,11 +590,11 @@ def run_batch(args, w, ctx, sub=False):
     m_s = float(peaks.get("hbm_gbs", M_S_FALLBACK))
     hbm_ach = bytes_alg / step_s / 1e9
     alu_peak = FP64_LANES_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 1e12
-    alu_ach = 5.0 * lups64 / step_s / 1e12
+    alu_ach = FP64_PIPE_ADDS * lups64 / step_s / 1e12
     if alu_ach / alu_peak > hbm_ach / m_s:
         roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
-                "traffic": None, "note": "FP64 pipe, 5 FP64 additions per FP64 LUP (the division runs on the "
-                "integer pipe); the launch also sweeps the FP32 grids",
+                "traffic": None, "note": "FP64 pipe, %d FP64-pipe additions per FP64 LUP (two additions and the "
+                "division run on the integer pipe); the launch also sweeps the FP32 grids" % FP64_PIPE_ADDS,
                 "hbm": {"achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s}}
     else:
         roof = {"bound": "hbm", "achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,

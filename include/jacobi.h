@@ -189,7 +189,7 @@ int jacobi_check_division(unsigned long long count, unsigned long long seed,
 
 /* Self-test of the exact FP64 addition that part of the FP64 sums use (the
  * additions of Eq. 1 moved to the integer pipe): compares it bit for bit
- * with the device's FP64 addition for 3*count pairs -- random bit patterns,
+ * with the device's FP64 addition for 4*count pairs -- random bit patterns,
  * and same-sign pairs whose exponents differ by 0..63 (carries, sticky
  * bits, ties) -- from SplitMix64 stream `seed`.  Synchronises the device.
  * *mismatches = differing results; first_bad[0..1] (may be NULL) = one

@@ -2,7 +2,11 @@
 
 Each translation unit is compiled in parallel to _build/*.o, then linked
 into paper_1006_3148_gb300/libjacobi.so (static CUDA runtime).  Rebuilds only
-when a source or header is newer than the library.
+when a source or header is newer than the library, or when the extra nvcc
+flags differ from the last build's.  Extra flags come from the environment
+variable JACOBI_NVCC_FLAGS (space separated), e.g.
+JACOBI_NVCC_FLAGS=-DJACOBI_INT_ADDS=0x00 for the build with every FP64
+addition on the FP64 pipe.
 """
 from __future__ import annotations
 
@@ -39,8 +43,23 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
 
 
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
+def extra_flags() -> list:
+    return os.environ.get("JACOBI_NVCC_FLAGS", "").split()
+
+
+def _stamped_flags() -> str:
+    try:
+        with open(STAMP) as fh:
+            return fh.read()
+    except OSError:
+        return ""
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or _stamped_flags() != " ".join(extra_flags()):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(d) <= t for d in _deps())
@@ -51,7 +70,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = extra_flags() + (["-Xptxas", "-v"] if ptxas_info else [])
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
@@ -71,6 +90,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(" ".join(extra_flags()))
     return LIB
 
 

@@ -7,6 +7,7 @@
 //   FP32: the sum is multiplied by RN_f32(1/6) (one multiplication and five
 //         additions, the count of Sect. 2.3).
 #pragma once
+#include <cstdint>
 
 namespace jac {
 
@@ -43,47 +44,82 @@ __device__ __forceinline__ double add_rn(double x, double y) { return __dadd_rn(
 
 // x + y in binary64, round to nearest even, computed on the integer pipe
 // (the FP64 pipe of this GPU retires at most 2 additions per SM per clock,
-// so part of the additions of a sweep can run here instead).  Fast path: both
-// operands finite and normal with biased exponent <= 2045, same sign; the
-// magnitudes are added (no cancellation) and rounded once:
-//   with |a| >= |b|, d = e_a - e_b: if d >= 54 then |b| < ulp(a)/2 and the
-//   result is a.  Otherwise the 53-bit significands are placed at bits
-//   62..10 of 64-bit words, b's shifted right by d with every bit shifted
-//   out kept as a sticky bit, the two added (< 2^64); a carry into bit 63
-//   shifts the sum right once (sticky kept) and raises the exponent; the
-//   low 10 bits then decide the round to nearest, ties to the even
-//   significand; a significand that rounds up to 2^53 carries into the
-//   exponent through the final addition of the exponent field.
-// Every other case (a zero, subnormal, huge, infinite or NaN operand, or
-// operands of opposite sign) uses the FP64 addition.  Checked bit for bit
-// against __dadd_rn by jacobi_check_addition.
+// so one of the five additions of a cell update can run here instead).
+// Sets ok = false where this path does not apply; the caller then adds on
+// the FP64 pipe.  It applies when both operands have the same sign, the
+// larger magnitude is a normal number below 2^1023 (biased exponent
+// 1..2045) and the smaller one is zero or normal with an exponent at most
+// 31 below it.  With |a| >= |b|, d = e_a - e_b, and 53-bit significands
+// M_a, M_b (hidden bit set), all in 32-bit words:
+//   the exact sum is M_a + M_b / 2^d; M_b >> d is two funnel shifts and the
+//   d bits shifted out form a 32-bit fraction F (left-aligned);
+//   S = M_a + (M_b >> d) lies in [2^52, 2^54); c = S >> 53 is its carry;
+//   the kept significand is S >> c, the guard bit the bit below it (bit 0
+//   of S if c, else the top bit of F) and the sticky bit the OR of the bits
+//   below the guard; round to nearest, ties to even, adds guard AND
+//   (sticky OR lowest kept bit); the result is sign | ((e_a + c - 1) << 52)
+//   plus the rounded significand, so a significand that rounds up to 2^53
+//   carries into the exponent by the addition itself.
+// A zero b gives a exactly (same sign).  Checked bit for bit against
+// __dadd_rn by jacobi_check_addition.
+__device__ __forceinline__ uint32_t shl_clamped(uint32_t v, uint32_t n)
+{
+    uint32_t r;  // PTX shl clamps shift counts above 32: 0 for n = 32
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(n));
+    return r;
+}
+
+__device__ __forceinline__ double add_rn_int_path(double x, double y, bool &ok)
+{
+    // 32-bit words only: a sign mask on the 64-bit pattern of a computed
+    // double would be turned into an FP64 absolute value by the compiler.
+    const uint32_t xh = (uint32_t)__double2hiint(x), xl = (uint32_t)__double2loint(x);
+    const uint32_t yh = (uint32_t)__double2hiint(y), yl = (uint32_t)__double2loint(y);
+    const uint32_t mx = xh & 0x7FFFFFFFu, my = yh & 0x7FFFFFFFu;
+    const bool sw = my > mx || (my == mx && yl > xl);
+    const uint32_t ah = sw ? yh : xh, al = sw ? yl : xl, bh = sw ? xh : yh, bl = sw ? xl : yl;  // |A| >= |B|
+    const uint32_t ea = (ah >> 20) & 0x7FFu, eb = (bh >> 20) & 0x7FFu, d = ea - eb;
+    const bool bzero = ((bh & 0x7FFFFFFFu) | bl) == 0u;
+    ok = ((ah ^ bh) >> 31) == 0u && ea - 1u < 2045u && (bzero || (eb != 0u && d < 32u));
+    const uint32_t mah = (ah & 0xFFFFFu) | 0x100000u, mbh = (bh & 0xFFFFFu) | 0x100000u;
+    const uint32_t dd = d & 31u;
+    const uint32_t ql = __funnelshift_r(bl, mbh, dd), qh = mbh >> dd;
+    const uint32_t F = shl_clamped(bl, 32u - dd);
+    const unsigned long long S = (((unsigned long long)mah << 32) | al) + (((unsigned long long)qh << 32) | ql);
+    const uint32_t sh = (uint32_t)(S >> 32), sl = (uint32_t)S;
+    const uint32_t c = sh >> 21;
+    const uint32_t Ml = __funnelshift_r(sl, sh, c), Mh = sh >> c;
+    const uint32_t g = c ? (sl & 1u) : (F >> 31);
+    const uint32_t sticky = (c ? F : (F << 1)) != 0u ? 1u : 0u;
+    const uint32_t ru = g & (sticky | (Ml & 1u));
+    const unsigned long long M = (((unsigned long long)Mh << 32) | Ml) + ru;
+    const uint32_t rh = (uint32_t)(M >> 32) + ((ea + c - 1u) << 20) + (ah & 0x80000000u), rl = (uint32_t)M;
+    return __hiloint2double((int)(bzero ? ah : rh), (int)(bzero ? al : rl));
+}
+
+// The same addition for one thread: the integer path, else the FP64 pipe.
 __device__ __forceinline__ double add_rn_int(double x, double y)
 {
-    const unsigned long long a0 = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long b0 = (unsigned long long)__double_as_longlong(y);
-    const unsigned ea0 = (unsigned)(a0 >> 52) & 0x7FFu, eb0 = (unsigned)(b0 >> 52) & 0x7FFu;
-    if (((a0 ^ b0) >> 63) != 0ull || ea0 - 1u > 2044u || eb0 - 1u > 2044u) return __dadd_rn(x, y);
-    const unsigned long long sign = a0 & 0x8000000000000000ull;
-    unsigned long long ua = a0 & 0x7FFFFFFFFFFFFFFFull, ub = b0 & 0x7FFFFFFFFFFFFFFFull;
-    if (ua < ub) {
-        const unsigned long long t = ua;
-        ua = ub;
-        ub = t;
+    bool ok;
+    const double r = add_rn_int_path(x, y, ok);
+    return ok ? r : __dadd_rn(x, y);
+}
+
+// FP64-pipe addition kept out of line: inlined, the compiler computes it
+// ahead of the branch that guards it.
+static __device__ __noinline__ double add_rn_outlined(double x, double y) { return __dadd_rn(x, y); }
+
+// In kernels: the integer path for every lane; the lanes it does not apply to
+// add on the FP64 pipe behind a warp vote, so warps with no such lane never
+// issue the FP64 instruction.
+__device__ __forceinline__ double add_rn_int_warp(double x, double y)
+{
+    bool ok;
+    double r = add_rn_int_path(x, y, ok);
+    if (__any_sync(__activemask(), !ok)) {
+        if (!ok) r = add_rn_outlined(x, y);
     }
-    const unsigned ea = (unsigned)(ua >> 52), d = ea - (unsigned)(ub >> 52);
-    if (d >= 54u) return __longlong_as_double((long long)(sign | ua));
-    const unsigned long long ma = ((ua & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) << 10;
-    const unsigned long long mb = ((ub & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) << 10;
-    unsigned long long s = ma + ((mb >> d) | ((mb & ((1ull << d) - 1ull)) != 0ull ? 1ull : 0ull));
-    unsigned e = ea;
-    if (s >> 63) {
-        s = (s >> 1) | (s & 1ull);
-        e += 1u;
-    }
-    unsigned long long q = s >> 10;
-    const unsigned r = (unsigned)s & 0x3FFu;
-    q += (r > 0x200u || (r == 0x200u && (q & 1ull))) ? 1ull : 0ull;
-    return __longlong_as_double((long long)(sign | ((((unsigned long long)(e - 1u)) << 52) + q)));
+    return r;
 }
 
 template <typename T>
@@ -91,14 +127,18 @@ struct Arith;
 
 // Which of the additions of Eq. (1) (bit i = addition i+1, left to right)
 // run on the integer pipe; the rest run on the FP64 pipe.  Both give the
-// identical IEEE result, so the split only balances the two pipes.
+// identical IEEE result, so the split only balances the two pipes.  The
+// first and the last (0x11): measured on the 512^3 FP64 workload, no
+// integer addition gives 104 GLUP/s (FP64 pipe 84 % busy, five additions
+// per cell), one 130, two 139 (three FP64 additions left), three 101 (the
+// integer ALU pipe then limits).
 #ifndef JACOBI_INT_ADDS
-#define JACOBI_INT_ADDS 0x00u
+#define JACOBI_INT_ADDS 0x11u
 #endif
 template <unsigned I>
 __device__ __forceinline__ double add_sel(double x, double y)
 {
-    return (JACOBI_INT_ADDS >> I) & 1u ? add_rn_int(x, y) : add_rn(x, y);
+    return (JACOBI_INT_ADDS >> I) & 1u ? add_rn_int_warp(x, y) : add_rn(x, y);
 }
 
 template <>

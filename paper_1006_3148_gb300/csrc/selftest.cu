@@ -66,9 +66,9 @@ __device__ void check_add(unsigned long long ba, unsigned long long bb, unsigned
     }
 }
 
-// Random pairs: independent bit patterns, and pairs with the same sign and
-// exponents a random distance 0..63 apart (the fast path's cases: carries,
-// sticky bits, ties).
+// Random pairs: independent bit patterns, pairs with the same sign and
+// exponents a random distance 0..63 apart (the integer path's cases up to
+// 31 apart: carries, sticky bits, ties) and a value plus a zero.
 __global__ void check_add_random(unsigned long long count, unsigned long long seed, unsigned long long *bad,
                                  unsigned long long *first)
 {
@@ -87,6 +87,8 @@ __global__ void check_add_random(unsigned long long count, unsigned long long se
         if ((r3 >> 20) & 1ull) b = (b & ~0xFFFFFFFFFull) | (1ull << ((r3 >> 21) % 36));  // sparse low bits: ties
         check_add(a, b, bad, first);
         check_add(b, a, bad, first);
+        // a zero of either sign against a random value
+        check_add(a, (r3 & 2ull) ? 0x8000000000000000ull : 0ull, bad, first);
     }
 }
 

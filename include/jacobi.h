@@ -218,9 +218,20 @@ int jacobi_profile_read(jacobi_h h, double *pass_ms, int *pass_launches, int *ot
 /* Test hook for failure detection: mode 1 makes the next pass kernel omit
  * one mbarrier arrival so that its bounded waits run out (after
  * limit_ms milliseconds); the kernel records JACOBI_ERR_TIMEOUT and returns
- * without faulting.  mode 0 disables it.  limit_ms also sets the wait limit
- * of later launches (default 2000). */
+ * without faulting.  Mode 2 (bounds-checked build only, else
+ * JACOBI_ERR_UNSUPPORTED): the kernels check their accesses against grids
+ * declared one element shorter than they are, so the accesses to each
+ * grid's last element are reported as JACOBI_ERR_BOUNDS and skipped (every
+ * skipped access is in fact valid: nothing faults).  mode 0 disables both.
+ * limit_ms also sets the wait limit of later launches (default 2000). */
 int jacobi_debug_set_fault(jacobi_h h, int mode, int limit_ms);
+
+/* 1 if this library is the bounds-checked build (compiled with
+ * -DJACOBI_CHECKED: every global, shared and distributed shared memory
+ * access of the sweep, batch and refinement kernels is checked against its
+ * buffer, and an access outside records JACOBI_ERR_BOUNDS in the status word
+ * and is skipped instead of performed), else 0. */
+int jacobi_build_checked(void);
 
 /* -------------------------------------------------------------- Poisson
  * -Lap_h u = f with the 7-point Laplacian, (A_h u) = (6u - sum of the six
@@ -350,7 +361,9 @@ int jacobi_batch_get_status(jacobi_batch_h b, int *device_status);
 /* Test hook: mode 1 makes the persistent kernel never publish sweep 2 of
  * the first tile, so that dependent waits run out after limit_ms and the
  * kernel records JACOBI_ERR_TIMEOUT (no fault); re-captures the graph.
- * Mode 1 needs the persistent engine (else JACOBI_ERR_UNSUPPORTED). */
+ * Mode 1 needs the persistent engine (else JACOBI_ERR_UNSUPPORTED).  Mode 2
+ * (bounds-checked build only): grids are checked as one element shorter than
+ * they are, as in jacobi_debug_set_fault. */
 int jacobi_batch_debug_set_fault(jacobi_batch_h b, int mode, int limit_ms);
 
 #ifdef __cplusplus

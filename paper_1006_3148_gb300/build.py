@@ -1,7 +1,8 @@
 """Builds libjacobi.so in-tree from csrc/*.cu for sm_103a (nvcc, no cmake).
 
 Each translation unit is compiled in parallel to _build/*.o, then linked
-into paper_1006_3148_gb300/libjacobi.so (static CUDA runtime).  Rebuilds only
+into paper_1006_3148_gb300/libjacobi.so (static CUDA runtime); a build tag
+(JACOBI_BUILD_TAG) selects another object folder and library name.  Rebuilds only
 when a source or header is newer than the library, or when the extra nvcc
 flags differ from the last build's.  Extra flags come from the environment
 variable JACOBI_NVCC_FLAGS (space separated), e.g.
@@ -19,8 +20,12 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(HERE, "libjacobi.so")
+# JACOBI_BUILD_TAG names a separate build (objects in _build_<tag>/, library
+# libjacobi_<tag>.so), e.g. "checked" with JACOBI_NVCC_FLAGS=-DJACOBI_CHECKED
+# for the bounds-checked library beside the normal one.
+TAG = os.environ.get("JACOBI_BUILD_TAG", "")
+BUILD = os.path.join(HERE, "_build" + ("_" + TAG if TAG else ""))
+LIB = os.path.join(HERE, "libjacobi" + ("_" + TAG if TAG else "") + ".so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

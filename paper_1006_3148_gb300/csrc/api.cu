@@ -13,6 +13,7 @@
 #include <tuple>
 #include <vector>
 
+#include "checked.cuh"
 #include "jacobi_internal.h"
 
 using namespace jac;
@@ -164,7 +165,7 @@ int check_plan(const jacobi_plan_s *h, const Plan &p)
 int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStream_t s)
 {
     if (T == 0) return JACOBI_OK;
-    cudaError_t e = halo_copy_launch(h->dtype, A, B, h->nx, h->ny, h->nz, s);
+    cudaError_t e = halo_copy_launch(h->dtype, A, B, h->nx, h->ny, h->nz, s, h->d_status, h->check_shrink);
     if (e != cudaSuccess) return cuda_fail(e);
     if (h->prof) ++h->prof_other;
     if (p.kernel == JACOBI_KERNEL_PLAIN || p.kernel == JACOBI_KERNEL_PLAIN_X2) {
@@ -175,6 +176,8 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
         a.kz = p.bz;
         a.tx = p.bx;
         a.ty = p.by;
+        a.status = h->d_status;
+        a.shrink = h->check_shrink;
         for (int t = 0; t < T; ++t) {
             a.src = (t % 2 == 0) ? A : B;
             a.dst = (t % 2 == 0) ? B : A;
@@ -195,6 +198,8 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
         a.ny = h->ny;
         a.nz = h->nz;
         a.bz = p.bz;
+        a.status = h->d_status;
+        a.shrink = h->check_shrink;
         for (int q = 0; q < P; ++q) {
             if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
             a.src = (q % 2 == 0) ? A : B;
@@ -212,6 +217,8 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
         a.ny = h->ny;
         a.nz = h->nz;
         a.bz = p.bz;
+        a.status = h->d_status;
+        a.shrink = h->check_shrink;
         for (int q = 0; q < P; ++q) {
             if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
             size_t smem = 0;
@@ -236,6 +243,7 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
     a.ntx = (h->nx + p.bx - 1) / p.bx;
     a.status = h->d_status;
     a.limit_ns = h->limit_ns;
+    a.shrink = h->check_shrink;
     TbLaunch L;
     int Ldepth = -1;
     for (int q = 0; q < P; ++q) {
@@ -437,11 +445,15 @@ int jacobi_get_status(jacobi_h h, int *device_status)
 
 int jacobi_debug_set_fault(jacobi_h h, int mode, int limit_ms)
 {
-    if (!h || mode < 0 || mode > 1 || limit_ms < 1) return JACOBI_ERR_ARG;
-    h->fault_mode = mode;
+    if (!h || mode < 0 || mode > 2 || limit_ms < 1) return JACOBI_ERR_ARG;
+    if (mode == 2 && !kChecked) return JACOBI_ERR_UNSUPPORTED;
+    h->fault_mode = (mode == 1) ? 1 : 0;
+    h->check_shrink = (mode == 2) ? 1 : 0;
     h->limit_ns = (unsigned long long)limit_ms * 1000000ull;
     return JACOBI_OK;
 }
+
+int jacobi_build_checked(void) { return kChecked ? 1 : 0; }
 
 int jacobi_profile_enable(jacobi_h h, int enable)
 {

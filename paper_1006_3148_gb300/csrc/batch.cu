@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "arith.cuh"
+#include "checked.cuh"
 #include "grid.cuh"
 #include "jacobi_internal.h"
 #include "ptx.cuh"
@@ -69,6 +70,7 @@ struct BatchArgs {
     int *status;
     unsigned long long limit_ns;
     int fault_mode;
+    long long shrink;  // checked build: grids declared this many elements short
 };
 
 namespace {
@@ -105,7 +107,8 @@ __device__ bool wait_progress(const int *progress, int i, int want, unsigned lon
 // the values at k-1, k, k+1 of its column in registers; in-plane neighbours
 // are read through L2 (.cg: other CTAs rewrote this buffer two sweeps ago).
 template <typename T>
-__device__ void sweep_tile(const BatchGrid &G, int tx, int ty, int tz, int p, int bx, int by, int bz)
+__device__ void sweep_tile(const BatchGrid &G, int tx, int ty, int tz, int p, int bx, int by, int bz, int *status,
+                           long long shrink)
 {
     const T *src = static_cast<const T *>((p % 2 == 0) ? G.A : G.B);
     T *dst = static_cast<T *>((p % 2 == 0) ? G.B : G.A);
@@ -114,21 +117,23 @@ __device__ void sweep_tile(const BatchGrid &G, int tx, int ty, int tz, int p, in
     const int nthreads = blockDim.x;
     const int x0 = 1 + tx * bx, y0 = 1 + ty * by, z0 = 1 + tz * bz;
     const int w = min(bx, G.nx + 1 - x0), hgt = min(by, G.ny + 1 - y0), z1 = min(z0 + bz, G.nz + 1);
+    const long long S = checked_grid_elems(G.nx, G.ny, G.nz, shrink);
+    auto ld = [&](const T *q) { return in_bounds(q - src, 1, S, status) ? __ldcg(q) : T(0); };
     for (int c = threadIdx.x; c < w * hgt; c += nthreads) {
         const int x = x0 + c % w, y = y0 + c / w;
         const T *col = src + (long long)y * NXP + x;
         T *ocol = dst + (long long)y * NXP + x;
-        T a = __ldcg(col + (long long)(z0 - 1) * plane), b = __ldcg(col + (long long)z0 * plane);
+        T a = ld(col + (long long)(z0 - 1) * plane), b = ld(col + (long long)z0 * plane);
         for (int k = z0; k < z1; ++k) {
             const T *cp = col + k * plane;
-            const T cnext = __ldcg(cp + plane);
+            const T cnext = ld(cp + plane);
             T v;
             if (rhs)
-                v = Arith<T>::update_rhs(__ldcg(cp - 1), __ldcg(cp + 1), __ldcg(cp - NXP), __ldcg(cp + NXP), a, cnext,
-                                         __ldg(rhs + (cp - src)));
+                v = Arith<T>::update_rhs(ld(cp - 1), ld(cp + 1), ld(cp - NXP), ld(cp + NXP), a, cnext,
+                                         in_bounds(cp - src, 1, S, status) ? __ldg(rhs + (cp - src)) : T(0));
             else
-                v = Arith<T>::update(__ldcg(cp - 1), __ldcg(cp + 1), __ldcg(cp - NXP), __ldcg(cp + NXP), a, cnext);
-            ocol[k * plane] = v;
+                v = Arith<T>::update(ld(cp - 1), ld(cp + 1), ld(cp - NXP), ld(cp + NXP), a, cnext);
+            if (in_bounds(ocol + k * plane - dst, 1, S, status)) ocol[k * plane] = v;
             a = b;
             b = cnext;
         }
@@ -176,8 +181,8 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs a)
         }
         __syncthreads();
         if (s_ok) {
-            if (G.dtype == JACOBI_F64) sweep_tile<double>(G, tx, ty, tz, p, a.bx, a.by, a.bz);
-            else sweep_tile<float>(G, tx, ty, tz, p, a.bx, a.by, a.bz);
+            if (G.dtype == JACOBI_F64) sweep_tile<double>(G, tx, ty, tz, p, a.bx, a.by, a.bz, a.status, a.shrink);
+            else sweep_tile<float>(G, tx, ty, tz, p, a.bx, a.by, a.bz, a.status, a.shrink);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs a)
 // units left, alternately a unit of the FP64 list (even b) and of the FP32
 // list (odd b); then the rest of the longer list.
 template <typename T, bool RHS>
-__device__ __forceinline__ void sweep_unit(const BatchGrid &G, int u, int p, int kz)
+__device__ __forceinline__ void sweep_unit(const BatchGrid &G, int u, int p, int kz, int *status, long long shrink)
 {
     const int r = u % G.nbxy, zc = u / G.nbxy;
     const int c = r * kSweepThreads + threadIdx.x;  // row-major interior cell of the plane
@@ -206,15 +211,23 @@ __device__ __forceinline__ void sweep_unit(const BatchGrid &G, int u, int p, int
     T *__restrict__ q = static_cast<T *>((p % 2 == 0) ? G.B : G.A) + c0;
     const T *__restrict__ g = RHS ? static_cast<const T *>(G.rhs) + c0 : nullptr;
     const int nxp = G.nx + 2;
-    T lo = __ldg(q0 - plane), mid = __ldg(q0);
+    // checked build: every element offset against the grid's extent
+    const T *sb = static_cast<const T *>((p % 2 == 0) ? G.A : G.B), *gb = static_cast<const T *>(G.rhs);
+    const T *db = static_cast<const T *>((p % 2 == 0) ? G.B : G.A);
+    const long long S = checked_grid_elems(G.nx, G.ny, G.nz, shrink);
+    auto ld = [&](const T *ptr, const T *base) { return in_bounds(ptr - base, 1, S, status) ? __ldg(ptr) : T(0); };
+    T lo = ld(q0 - plane, sb), mid = ld(q0, sb);
 #pragma unroll 4
     for (int k = kb; k < ke; ++k) {
-        const T hi = __ldg(q0 + plane);
+        const T hi = ld(q0 + plane, sb);
         if (RHS) {
-            *q = Arith<T>::update_rhs(__ldg(q0 - 1), __ldg(q0 + 1), __ldg(q0 - nxp), __ldg(q0 + nxp), lo, hi, __ldg(g));
+            const T v = Arith<T>::update_rhs(ld(q0 - 1, sb), ld(q0 + 1, sb), ld(q0 - nxp, sb), ld(q0 + nxp, sb), lo, hi,
+                                             ld(g, gb));
+            if (in_bounds(q - db, 1, S, status)) *q = v;
             g += plane;
         } else {
-            *q = Arith<T>::update(__ldg(q0 - 1), __ldg(q0 + 1), __ldg(q0 - nxp), __ldg(q0 + nxp), lo, hi);
+            const T v = Arith<T>::update(ld(q0 - 1, sb), ld(q0 + 1, sb), ld(q0 - nxp, sb), ld(q0 + nxp, sb), lo, hi);
+            if (in_bounds(q - db, 1, S, status)) *q = v;
         }
         lo = mid;
         mid = hi;
@@ -225,7 +238,8 @@ __device__ __forceinline__ void sweep_unit(const BatchGrid &G, int u, int p, int
 
 __global__ void __launch_bounds__(kSweepThreads) batch_sweep_kernel(const BatchGrid *grids,
                                                                          const SweepEntry *tab, int n64, int n32,
-                                                                         long long u64, long long u32, int p, int kz)
+                                                                         long long u64, long long u32, int p, int kz,
+                                                                         int *status, long long shrink)
 {
     const long long b = blockIdx.x + (long long)gridDim.x * blockIdx.y;
     const long long m = u64 < u32 ? u64 : u32;
@@ -252,23 +266,25 @@ __global__ void __launch_bounds__(kSweepThreads) batch_sweep_kernel(const BatchG
     // element type and source term are uniform per block: the plane loop is
     // instantiated for each combination
     if (list == 0) {
-        if (G.rhs) sweep_unit<double, true>(G, u, p, kz);
-        else sweep_unit<double, false>(G, u, p, kz);
+        if (G.rhs) sweep_unit<double, true>(G, u, p, kz, status, shrink);
+        else sweep_unit<double, false>(G, u, p, kz, status, shrink);
     } else {
-        if (G.rhs) sweep_unit<float, true>(G, u, p, kz);
-        else sweep_unit<float, false>(G, u, p, kz);
+        if (G.rhs) sweep_unit<float, true>(G, u, p, kz, status, shrink);
+        else sweep_unit<float, false>(G, u, p, kz, status, shrink);
     }
 }
 
 // Copies the halo of A into B for every grid (blockIdx.y = grid).
-__global__ void batch_halo_kernel(const BatchGrid *grids)
+__global__ void batch_halo_kernel(const BatchGrid *grids, int *status, long long shrink)
 {
     const BatchGrid G = grids[blockIdx.y];
     if (G.T <= 0) return;
     const long long total = halo_count(G.nx, G.ny, G.nz);
+    const long long S = checked_grid_elems(G.nx, G.ny, G.nz, shrink);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long i = halo_cell(t, G.nx, G.ny, G.nz);
+        if (!in_bounds(i, 1, S, status)) continue;
         if (G.dtype == JACOBI_F64) static_cast<double *>(G.B)[i] = static_cast<const double *>(G.A)[i];
         else static_cast<float *>(G.B)[i] = static_cast<const float *>(G.A)[i];
     }
@@ -297,6 +313,7 @@ struct jacobi_batch_s {
     cudaGraphExec_t exec = nullptr;
     int fault_mode = 0;
     unsigned long long limit_ns = 2000000000ull;
+    long long check_shrink = 0;  // checked build test hook (debug mode 2)
     bool bound = false;
 };
 
@@ -392,6 +409,7 @@ int build_graph(jacobi_batch_s *b)
     a.progress = b->d_ctl + 2;
     a.limit_ns = b->limit_ns;
     a.fault_mode = b->fault_mode;
+    a.shrink = b->check_shrink;
 
     if (b->engine == JACOBI_BATCH_SWEEPS) {
         const std::vector<SweepEntry> tab = sweep_table(b);
@@ -411,14 +429,14 @@ int build_graph(jacobi_batch_s *b)
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         if (b->engine == JACOBI_BATCH_SWEEPS) {
-            batch_halo_kernel<<<dim3(64, (unsigned)b->n), 256, 0, cs>>>(b->d_grids);
+            batch_halo_kernel<<<dim3(64, (unsigned)b->n), 256, 0, cs>>>(b->d_grids, a.status, a.shrink);
             for (int p = 0; p < b->max_T; ++p)
                 batch_sweep_kernel<<<dim3(gx, gy), kSweepThreads, 0, cs>>>(
-                    b->d_grids, b->d_tab, b->n64, b->n32, b->u64, b->u32, p, b->kz);
+                    b->d_grids, b->d_tab, b->n64, b->n32, b->u64, b->u32, p, b->kz, a.status, a.shrink);
         } else {
             cudaMemsetAsync(b->d_ctl, 0, sizeof(int), cs);
             cudaMemsetAsync(b->d_ctl + 2, 0, sizeof(int) * (size_t)b->total_tiles, cs);
-            batch_halo_kernel<<<dim3(64, (unsigned)b->n), 256, 0, cs>>>(b->d_grids);
+            batch_halo_kernel<<<dim3(64, (unsigned)b->n), 256, 0, cs>>>(b->d_grids, a.status, a.shrink);
             batch_kernel<<<b->persistent_blocks, 256, 0, cs>>>(a);
         }
         e = cudaStreamEndCapture(cs, &b->graph);
@@ -570,9 +588,11 @@ int jacobi_batch_get_status(jacobi_batch_h b, int *device_status)
 
 int jacobi_batch_debug_set_fault(jacobi_batch_h b, int mode, int limit_ms)
 {
-    if (!b || mode < 0 || mode > 1 || limit_ms < 1) return JACOBI_ERR_ARG;
+    if (!b || mode < 0 || mode > 2 || limit_ms < 1) return JACOBI_ERR_ARG;
     if (mode == 1 && b->engine != JACOBI_BATCH_PERSISTENT) return JACOBI_ERR_UNSUPPORTED;
-    b->fault_mode = mode;
+    if (mode == 2 && !kChecked) return JACOBI_ERR_UNSUPPORTED;
+    b->fault_mode = (mode == 1) ? 1 : 0;
+    b->check_shrink = (mode == 2) ? 1 : 0;
     b->limit_ns = (unsigned long long)limit_ms * 1000000ull;
     return build_graph(b);
 }

@@ -24,6 +24,7 @@ struct TbArgs {
     int *status;        // device status word (first error code wins)
     unsigned long long limit_ns;  // bound of every device-side wait
     int fault_mode;     // test hook: 1 = drop one arrival (see jacobi.h)
+    long long shrink = 0;  // checked build: grids declared this many elements short
 };
 
 // Arguments of one pass of the one-CTA temporally blocked kernel.
@@ -33,6 +34,8 @@ struct TbcArgs {
     int nx, ny, nz;
     int bx, by, bz;  // tile interior (x, y) and z chunk
     int W, H, WH;    // region: tile widened by the depth on each side
+    int *status = nullptr;  // checked build: bounds errors
+    long long shrink = 0;
 };
 
 // Arguments of one pass of the register-blocked one-CTA kernel (FP32).
@@ -46,6 +49,8 @@ struct TbrArgs {
     int bx, by, bz;  // output tile (x, y) and z chunk
     int x_first;     // region origin of tile 0: 1 - D - off
     int off;         // alignment slack left of the region's margin
+    int *status = nullptr;  // checked build: bounds errors
+    long long shrink = 0;
 };
 
 struct PlainArgs {
@@ -56,6 +61,8 @@ struct PlainArgs {
     int kz;      // planes per thread
     int tx, ty;  // CTA shape in cells
     int gy, gz;  // row blocks, z chunks (set by plain_launch)
+    int *status = nullptr;  // checked build: bounds errors
+    long long shrink = 0;
 };
 
 // Plan of one handle.
@@ -103,7 +110,8 @@ cudaError_t tbr_launch(int depth, int W, int H, const TbrArgs &a, cudaStream_t s
 cudaError_t tbr_launch_a1(int depth, int W, int H, const TbrArgs &a, size_t smem, cudaStream_t s);
 cudaError_t tbr_launch_a2(int depth, int W, int H, const TbrArgs &a, size_t smem, cudaStream_t s);
 cudaError_t fill_launch(int dtype, void *p, long long n, double v, cudaStream_t s);
-cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, int nz, cudaStream_t s);
+cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, int nz, cudaStream_t s,
+                             int *status = nullptr, long long shrink = 0);
 
 // Pass planning: split T sweeps into passes of depth <= d whose count has
 // the parity of T (so the result ends in the grid single sweeps would use).
@@ -124,6 +132,7 @@ struct jacobi_plan_s {
     std::vector<cudaEvent_t> ev_pool;           // events, reused after a read
     size_t ev_used = 0;
     int prof_pass = 0, prof_other = 0;
+    long long check_shrink = 0;  // checked build test hook (jacobi_debug_set_fault mode 2)
     // Poisson / refinement scratch (allocated on first use, freed by destroy)
     void *g = nullptr;          // source term h^2 r (FP32) or h^2 f (FP64)
     void *e0 = nullptr, *e1 = nullptr;  // FP32 correction grids

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "checked.cuh"
 #include "jacobi_internal.h"
 
 namespace jac {
@@ -46,12 +47,14 @@ __device__ __forceinline__ long long cell_index(long long c, int nx, int ny)
 
 // partials[b] = sum of f^2 over the cells of block b.
 __global__ void __launch_bounds__(kRedThreads) sumsq_kernel(const double *f, int nx, int ny, int nz,
-                                                            double *partials)
+                                                            double *partials, int *status, long long shrink)
 {
     const long long n = (long long)nx * ny * nz;
+    const long long S = checked_grid_elems(nx, ny, nz, shrink);
     double acc = 0.0;
     for (long long c = blockIdx.x * (long long)kRedThreads + threadIdx.x; c < n; c += (long long)kRedBlocks * kRedThreads) {
-        const double v = f[cell_index(c, nx, ny)];
+        const long long i = cell_index(c, nx, ny);
+        const double v = in_bounds(i, 1, S, status) ? f[i] : 0.0;
         acc = __fma_rn(v, v, acc);
     }
     const double t = block_sum(acc);
@@ -63,21 +66,23 @@ __global__ void __launch_bounds__(kRedThreads) sumsq_kernel(const double *f, int
 // source term of the correction, g = RN_f32(h^2 r); partial sums of r^2.
 __global__ void __launch_bounds__(kRedThreads) residual_kernel(const double *u, const double *f, float *g, int nx,
                                                                int ny, int nz, double h2, double inv_h2,
-                                                               double *partials)
+                                                               double *partials, int *status, long long shrink)
 {
     const long long n = (long long)nx * ny * nz;
     const long long NXP = nx + 2, plane = NXP * (ny + 2);
+    const long long S = checked_grid_elems(nx, ny, nz, shrink);
+    auto U = [&](long long i) { return in_bounds(i, 1, S, status) ? u[i] : 0.0; };
     double acc = 0.0;
     for (long long c = blockIdx.x * (long long)kRedThreads + threadIdx.x; c < n; c += (long long)kRedBlocks * kRedThreads) {
         const long long i = cell_index(c, nx, ny);
-        double s = __dadd_rn(u[i - 1], u[i + 1]);
-        s = __dadd_rn(s, u[i - NXP]);
-        s = __dadd_rn(s, u[i + NXP]);
-        s = __dadd_rn(s, u[i - plane]);
-        s = __dadd_rn(s, u[i + plane]);
-        const double au = __dmul_rn(__dsub_rn(__dmul_rn(6.0, u[i]), s), inv_h2);
-        const double r = __dsub_rn(f[i], au);
-        if (g) g[i] = __double2float_rn(__dmul_rn(h2, r));
+        double s = __dadd_rn(U(i - 1), U(i + 1));
+        s = __dadd_rn(s, U(i - NXP));
+        s = __dadd_rn(s, U(i + NXP));
+        s = __dadd_rn(s, U(i - plane));
+        s = __dadd_rn(s, U(i + plane));
+        const double au = __dmul_rn(__dsub_rn(__dmul_rn(6.0, U(i)), s), inv_h2);
+        const double r = __dsub_rn(in_bounds(i, 1, S, status) ? f[i] : 0.0, au);
+        if (g && in_bounds(i, 1, S, status)) g[i] = __double2float_rn(__dmul_rn(h2, r));
         acc = __fma_rn(r, r, acc);
     }
     const double t = block_sum(acc);
@@ -94,22 +99,25 @@ __global__ void reduce_partials_kernel(const double *partials, int n, double *ou
 }
 
 // u += (double) e on the interior.
-__global__ void update_kernel(double *u, const float *e, int nx, int ny, int nz)
+__global__ void update_kernel(double *u, const float *e, int nx, int ny, int nz, int *status, long long shrink)
 {
     const long long n = (long long)nx * ny * nz;
+    const long long S = checked_grid_elems(nx, ny, nz, shrink);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const long long i = cell_index(c, nx, ny);
-        u[i] = __dadd_rn(u[i], (double)e[i]);
+        if (in_bounds(i, 1, S, status)) u[i] = __dadd_rn(u[i], (double)e[i]);
     }
 }
 
 // g = h^2 f (FP64) on the interior.
-__global__ void scale_kernel(const double *f, double *g, double h2, int nx, int ny, int nz)
+__global__ void scale_kernel(const double *f, double *g, double h2, int nx, int ny, int nz, int *status,
+                             long long shrink)
 {
     const long long n = (long long)nx * ny * nz;
+    const long long S = checked_grid_elems(nx, ny, nz, shrink);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const long long i = cell_index(c, nx, ny);
-        g[i] = __dmul_rn(h2, f[i]);
+        if (in_bounds(i, 1, S, status)) g[i] = __dmul_rn(h2, f[i]);
     }
 }
 
@@ -136,6 +144,8 @@ PlainArgs inner_args(const jacobi_plan_s *h, int dtype, const void *rhs, bool *x
     a.rhs = rhs;
     a.tx = 32;
     a.ty = 8;
+    a.status = h->d_status;
+    a.shrink = h->check_shrink;
     *x2 = (dtype == JACOBI_F32 && h->nx % 2 == 0);
     const long long row = *x2 ? 32ll * (((h->nx + 2) / 2 + 31) / 32) : 32ll * ((h->nx + 31) / 32);
     const long long want = 2ll * std::max(h->sms, 1) * 2048;
@@ -236,7 +246,8 @@ int residual_norm(jacobi_plan_s *h, const double *u, const double *f, float *g, 
                   double *rnorm)
 {
     const double h2 = hgrid * hgrid;
-    residual_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(u, f, g, h->nx, h->ny, h->nz, h2, 1.0 / h2, h->partials);
+    residual_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(u, f, g, h->nx, h->ny, h->nz, h2, 1.0 / h2, h->partials,
+                                                       h->d_status, h->check_shrink);
     if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
     if (h->prof) h->prof_other += 1;
     return read_norm(h, s, rnorm);
@@ -244,7 +255,8 @@ int residual_norm(jacobi_plan_s *h, const double *u, const double *f, float *g, 
 
 int f_norm(jacobi_plan_s *h, const double *f, cudaStream_t s, double *fnorm)
 {
-    sumsq_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(f, h->nx, h->ny, h->nz, h->partials);
+    sumsq_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(f, h->nx, h->ny, h->nz, h->partials, h->d_status,
+                                                    h->check_shrink);
     if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
     if (h->prof) h->prof_other += 1;
     return read_norm(h, s, fnorm);
@@ -298,9 +310,10 @@ int jacobi_poisson_jacobi(jacobi_h h, void *u, void *tmp, const void *f, double 
     cudaStream_t s = (cudaStream_t)stream;
     if (!h->g && cudaMalloc(&h->g, cells(h) * sizeof(double)) != cudaSuccess) return JACOBI_ERR_ALLOC;
     scale_kernel<<<608, 256, 0, s>>>(static_cast<const double *>(f), static_cast<double *>(h->g), hgrid * hgrid,
-                                     h->nx, h->ny, h->nz);
+                                     h->nx, h->ny, h->nz, h->d_status, h->check_shrink);
     if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
-    if (halo_copy_launch(JACOBI_F64, u, tmp, h->nx, h->ny, h->nz, s) != cudaSuccess) return JACOBI_ERR_CUDA;
+    if (halo_copy_launch(JACOBI_F64, u, tmp, h->nx, h->ny, h->nz, s, h->d_status, h->check_shrink) != cudaSuccess)
+        return JACOBI_ERR_CUDA;
     if (h->prof) h->prof_other += 2;  // scale, halo copy
     return run_inner(h, JACOBI_F64, sweeps, u, tmp, h->g, s);
 }
@@ -338,7 +351,7 @@ int jacobi_refine(jacobi_h h, double *u, const double *f, double hgrid, double r
         st = run_inner(h, JACOBI_F32, inner_sweeps, h->e0, h->e1, h->g, s);
         if (st != JACOBI_OK) return st;
         const float *e = static_cast<const float *>((inner_sweeps % 2 == 0) ? h->e0 : h->e1);
-        update_kernel<<<608, 256, 0, s>>>(u, e, h->nx, h->ny, h->nz);
+        update_kernel<<<608, 256, 0, s>>>(u, e, h->nx, h->ny, h->nz, h->d_status, h->check_shrink);
         if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
         if (h->prof) h->prof_other += 1;  // update
         ++outer;

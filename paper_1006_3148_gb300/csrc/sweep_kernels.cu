@@ -26,6 +26,7 @@
 #include <type_traits>
 
 #include "arith.cuh"
+#include "checked.cuh"
 #include "grid.cuh"
 #include "jacobi_internal.h"
 #include "ptx.cuh"
@@ -34,13 +35,15 @@ namespace jac {
 
 // ------------------------------------------------------------------ halo
 template <typename T>
-__global__ void halo_copy_kernel(const T *__restrict__ A, T *__restrict__ B, int nx, int ny, int nz)
+__global__ void halo_copy_kernel(const T *__restrict__ A, T *__restrict__ B, int nx, int ny, int nz, int *status,
+                                 long long shrink)
 {
     const long long total = halo_count(nx, ny, nz);
+    const long long S = checked_grid_elems(nx, ny, nz, shrink);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long idx = halo_cell(t, nx, ny, nz);
-        B[idx] = A[idx];
+        if (in_bounds(idx, 1, S, status)) B[idx] = A[idx];
     }
 }
 
@@ -79,15 +82,23 @@ __global__ void __launch_bounds__(1024) plain_pass_kernel(const PlainArgs a)
     T *__restrict__ q = static_cast<T *>(a.dst) + c0;
     const T *__restrict__ g = RHS ? static_cast<const T *>(a.rhs) + c0 : nullptr;
     const int nxp = a.nx + 2;
-    T lo = __ldg(p - plane), mid = __ldg(p);
+    // checked build: every element offset against the grid's extent
+    const T *sb = static_cast<const T *>(a.src), *gb = static_cast<const T *>(a.rhs);
+    const T *db = static_cast<const T *>(a.dst);
+    const long long S = checked_grid_elems(a.nx, a.ny, a.nz, a.shrink);
+    auto ld = [&](const T *ptr, const T *base) { return in_bounds(ptr - base, 1, S, a.status) ? __ldg(ptr) : T(0); };
+    T lo = ld(p - plane, sb), mid = ld(p, sb);
 #pragma unroll 4
     for (int k = kb; k < ke; ++k) {
-        const T hi = __ldg(p + plane);
+        const T hi = ld(p + plane, sb);
         if (RHS) {
-            *q = Arith<T>::update_rhs(__ldg(p - 1), __ldg(p + 1), __ldg(p - nxp), __ldg(p + nxp), lo, hi, __ldg(g));
+            const T v = Arith<T>::update_rhs(ld(p - 1, sb), ld(p + 1, sb), ld(p - nxp, sb), ld(p + nxp, sb), lo, hi,
+                                             ld(g, gb));
+            if (in_bounds(q - db, 1, S, a.status)) *q = v;
             g += plane;
         } else {
-            *q = Arith<T>::update(__ldg(p - 1), __ldg(p + 1), __ldg(p - nxp), __ldg(p + nxp), lo, hi);
+            const T v = Arith<T>::update(ld(p - 1, sb), ld(p + 1, sb), ld(p - nxp, sb), ld(p + nxp, sb), lo, hi);
+            if (in_bounds(q - db, 1, S, a.status)) *q = v;
         }
         lo = mid;
         mid = hi;
@@ -176,22 +187,30 @@ __global__ void __launch_bounds__(1024) plain_x2_kernel(const PlainArgs a)
     V zero;
     zero.x = T(0);
     zero.y = T(0);
+    // checked build: every element offset against the grid's extent
+    const T *sb = static_cast<const T *>(a.src), *gb = static_cast<const T *>(a.rhs);
+    const T *db = static_cast<const T *>(a.dst);
+    const long long S = checked_grid_elems(a.nx, a.ny, a.nz, a.shrink);
+    auto ld2 = [&](const V *ptr, const T *base) {
+        return in_bounds(reinterpret_cast<const T *>(ptr) - base, 2, S, a.status) ? __ldg(ptr) : zero;
+    };
+    auto ld1 = [&](const T *ptr) { return in_bounds(ptr - sb, 1, S, a.status) ? __ldg(ptr) : T(0); };
     const bool left_halo = (m == 0), right_halo = (2 * m + 1 == a.nx + 1);
-    V lo = live ? __ldg(p2 - P2) : zero, mid = live ? __ldg(p2) : zero;
+    V lo = live ? ld2(p2 - P2, sb) : zero, mid = live ? ld2(p2, sb) : zero;
 #pragma unroll 4
     for (int k = kb; k < ke; ++k) {
         V hi = zero, ym = zero, yp = zero, gv = zero;
         T w = T(0), e = T(0);
         if (live) {
-            hi = __ldg(p2 + P2);
-            if (RHS) gv = __ldg(g2);
-            ym = __ldg(p2 - R2);
-            yp = __ldg(p2 + R2);
+            hi = ld2(p2 + P2, sb);
+            if (RHS) gv = ld2(g2, gb);
+            ym = ld2(p2 - R2, sb);
+            yp = ld2(p2 + R2, sb);
             // Cells beyond the pair at the warp's ends.  For pair 0 the cell
             // left of x = 0 is the previous row's last halo cell (in the
             // array, result unused); likewise right of x = nx+1.
-            if (lane == 0) w = __ldg(p - 1);
-            if (lane == 31) e = __ldg(p + 2);
+            if (lane == 0) w = ld1(p - 1);
+            if (lane == 31) e = ld1(p + 2);
         }
         const T wl = __shfl_up_sync(0xffffffffu, mid.y, 1);
         const T er = __shfl_down_sync(0xffffffffu, mid.x, 1);
@@ -200,7 +219,7 @@ __global__ void __launch_bounds__(1024) plain_x2_kernel(const PlainArgs a)
         V o = RHS ? Pair<T>::update_rhs(w, mid, e, ym, yp, lo, hi, gv) : Pair<T>::update(w, mid, e, ym, yp, lo, hi);
         if (left_halo) o.x = mid.x;
         if (right_halo) o.y = mid.y;
-        if (live) *q2 = o;
+        if (live && in_bounds(reinterpret_cast<const T *>(q2) - db, 2, S, a.status)) *q2 = o;
         lo = mid;
         mid = hi;
         p2 += P2;
@@ -383,7 +402,8 @@ cudaError_t plain_x2_launch(int dtype, PlainArgs a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, int nz, cudaStream_t s)
+cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, int nz, cudaStream_t s, int *status,
+                             long long shrink)
 {
     const long long total = halo_count(nx, ny, nz);
     const int block = 256;
@@ -391,10 +411,10 @@ cudaError_t halo_copy_launch(int dtype, const void *A, void *B, int nx, int ny, 
     const unsigned grid = (unsigned)std::min<long long>(want, 152 * 16);
     if (dtype == JACOBI_F64)
         halo_copy_kernel<double><<<grid, block, 0, s>>>(static_cast<const double *>(A), static_cast<double *>(B), nx,
-                                                          ny, nz);
+                                                          ny, nz, status, shrink);
     else
         halo_copy_kernel<float><<<grid, block, 0, s>>>(static_cast<const float *>(A), static_cast<float *>(B), nx, ny,
-                                                        nz);
+                                                        nz, status, shrink);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 #include <type_traits>
 
 #include "arith.cuh"
+#include "checked.cuh"
 #include "jacobi_internal.h"
 #include "ptx.cuh"
 
@@ -103,6 +104,12 @@ __global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_
     const int lane = tid & 31, warp = tid >> 5;
     const volatile int *vstatus = a.status;
     const long long plane = (long long)NYP * NXP;
+    // checked build: global offsets against the grid, ring indices (this
+    // CTA's or, for the hand-off, the next CTA's) against the ring slots
+    const long long SG = checked_grid_elems(nx, ny, nz, a.shrink);
+    const long long SR = (long long)R * slot_elems;
+    auto gok = [&](long long off, int cnt) { return in_bounds(off, cnt, SG, a.status); };
+    auto rok = [&](long long idx, int cnt) { return in_bounds(idx, cnt, SR, a.status); };
 
     const int wl = D - lvl;  // this level's region is the tile widened by wl
     const int zo0 = max(z0 - wl, 0), zo1 = min(z1 + wl, nz + 2);
@@ -191,6 +198,12 @@ __global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_
                     const uint32_t d = sb + (uint32_t)((yl * Wp + xl) * (int)sizeof(T));
                     const T *g = gp + (yl * NXP + xl);
                     const uint32_t lg = pc >> 28;
+                    if (kChecked) {
+                        const int cnt = (4 << lg) / (int)sizeof(T);
+                        if (!rok((long long)slot * slot_elems + yl * Wp + xl, cnt) ||
+                            !gok((long long)(zi0 + n) * plane + (long long)(ys + yl) * NXP + xs + xl, cnt))
+                            continue;
+                    }
                     if (lg == 2) cp_async_16(d, g);
                     else if (lg == 1) cp_async_8(d, g);
                     else cp_async_4(d, g);
@@ -201,6 +214,9 @@ __global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_
                     const T *grow = gp + (long long)(y - ys) * NXP - xs;
                     const uint32_t srow = sb + (uint32_t)(((y - ys) * Wp - xs) * (int)sizeof(T));
                     for (int x = ix0 + lane; x < ix1; x += 32) {
+                        if (kChecked && (!rok((long long)slot * slot_elems + (y - ys) * Wp - xs + x, 1) ||
+                                         !gok((long long)(zi0 + n) * plane + (long long)y * NXP + x, 1)))
+                            continue;
                         if (sizeof(T) == 8) cp_async_8(srow + (uint32_t)x * 8u, grow + x);
                         else cp_async_4(srow + (uint32_t)x * 4u, grow + x);
                     }
@@ -258,7 +274,8 @@ __global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_
         }
     };
     auto ldv = [&](const T *p, T (&v)[VEC]) {
-        const V t = *reinterpret_cast<const V *>(p);
+        V t = V();
+        if (rok(p - ring, VEC)) t = *reinterpret_cast<const V *>(p);
         if constexpr (VEC == 4) {
             v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
         } else {
@@ -322,7 +339,7 @@ __global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_
                 T sv[VEC], nv[VEC];
                 ldv(c - Wp, sv);
                 ldv(c + Wp, nv);
-                const T wv = c[-1], ev = c[VEC];
+                const T wv = rok(c - 1 - ring, 1) ? c[-1] : T(0), ev = rok(c + VEC - ring, 1) ? c[VEC] : T(0);
 #pragma unroll
                 for (int l = 0; l < VEC; ++l) {
                     const T left = (l == 0) ? wv : B[q][l - 1];
@@ -335,9 +352,19 @@ __global__ void __launch_bounds__(NC, (NC == 512 ? 2 : (NC == 128 ? 3 : 2))) tb_
                 for (int l = 0; l < VEC; ++l) v[l] = B[q][l];
             }
             if (lvl < D) {
-                st_async_v(out_base + (uint32_t)goff[q] * (uint32_t)sizeof(T), v, out_bar);
+                // in the checked build a skipped hand-off leaves the consumer
+                // short of bytes: its bounded wait then ends with a timeout
+                if (rok((long long)(m & rmask) * slot_elems + goff[q], VEC))
+                    st_async_v(out_base + (uint32_t)goff[q] * (uint32_t)sizeof(T), v, out_bar);
             } else {
                 T *gpo = drow + gofs[q];
+                if (kChecked && !gok((long long)k * plane + gofs[q], VEC)) {
+                    // a group partly outside the grid: store its lanes one by one
+#pragma unroll
+                    for (int l = 0; l < VEC; ++l)
+                        if ((f & (256u << l)) && gok((long long)k * plane + gofs[q] + l, 1)) gpo[l] = v[l];
+                    continue;
+                }
                 const bool full = (f & (((1u << VEC) - 1u) << 8)) == (((1u << VEC) - 1u) << 8);
                 if (full && cs == VEC) {
                     V t;

@@ -29,6 +29,7 @@
 #include <algorithm>
 
 #include "arith.cuh"
+#include "checked.cuh"
 #include "jacobi_internal.h"
 #include "ptx.cuh"
 
@@ -50,6 +51,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) tbc_pass_kernel(const T
     const int z0 = 1 + blockIdx.z * a.bz, z1 = min(z0 + a.bz, a.nz + 1);
     const T *__restrict__ src = static_cast<const T *>(a.src);
     T *__restrict__ dst = static_cast<T *>(a.dst);
+    // checked build: global offsets against the grid, shared indices against
+    // the ring and level planes
+    const long long SG = checked_grid_elems(a.nx, a.ny, a.nz, a.shrink);
+    const long long SS = (long long)(kRing + 2 * (D - 1)) * WH;
+    auto gok = [&](long long off) { return in_bounds(off, 1, SG, a.status); };
+    auto sok = [&](const T *ptr) { return in_bounds(ptr - ring, 1, SS, a.status); };
+    auto lds = [&](const T *ptr) { return sok(ptr) ? *ptr : T(0); };
 
     // Owned cells: c = tid + r*NT of the W x H region.
     int cell[CPT];
@@ -70,7 +78,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) tbc_pass_kernel(const T
         flags |= (store ? 1u : 0u) << (4 * r + 2);
         flags |= (valid ? 1u : 0u) << (4 * r + 3);
     }
-    for (int c = tid; c < 2 * (D - 1) * WH; c += NT) lev[c] = T(0);
+    for (int c = tid; c < 2 * (D - 1) * WH; c += NT)
+        if (sok(lev + c)) lev[c] = T(0);
 
     // Input plane p (if inside the array's planes) into its ring slot.
     auto load_plane = [&](int p) {
@@ -78,7 +87,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) tbc_pass_kernel(const T
             T *slot = ring + (p & (kRing - 1)) * WH;
             const T *sp = src + (long long)p * plane;
             for (int r = 0; r < CPT; ++r) {
-                if (flags & (1u << (4 * r))) {
+                if ((flags & (1u << (4 * r))) && sok(slot + cell[r]) && gok((long long)p * plane + goff[r])) {
                     const uint32_t d = smem_addr(slot + cell[r]);
                     if (sizeof(T) == 8) cp_async_8(d, sp + goff[r]);
                     else cp_async_4(d, sp + goff[r]);
@@ -98,8 +107,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) tbc_pass_kernel(const T
     cp_async_wait_group<0>();
     __syncthreads();
     for (int r = 0; r < CPT; ++r) {
-        q0[0][r] = ring[((s_begin - 1) & (kRing - 1)) * WH + cell[r]];
-        q1[0][r] = ring[(s_begin & (kRing - 1)) * WH + cell[r]];
+        q0[0][r] = lds(ring + ((s_begin - 1) & (kRing - 1)) * WH + cell[r]);
+        q1[0][r] = lds(ring + (s_begin & (kRing - 1)) * WH + cell[r]);
 #pragma unroll
         for (int l = 1; l < D; ++l) {
             q0[l][r] = T(0);
@@ -114,7 +123,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) tbc_pass_kernel(const T
         load_plane(s + 3);         // into the slot of plane s-1, read for the last time in step s-1
         T up[CPT];                 // level l-1 at plane p+1 (this step)
         const T *inb = ring + ((s + 1) & (kRing - 1)) * WH;
-        for (int r = 0; r < CPT; ++r) up[r] = inb[cell[r]];
+        for (int r = 0; r < CPT; ++r) up[r] = lds(inb + cell[r]);
 #pragma unroll
         for (int l = 1; l <= D; ++l) {
             const int p = s - l + 1;
@@ -124,7 +133,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) tbc_pass_kernel(const T
                 const int c = cell[r];
                 T v;
                 if (zin && (flags & (2u << (4 * r))))
-                    v = Arith<T>::update(nb[c - 1], nb[c + 1], nb[c - W], nb[c + W], q0[l - 1][r], up[r]);
+                    v = Arith<T>::update(lds(nb + c - 1), lds(nb + c + 1), lds(nb + c - W), lds(nb + c + W), q0[l - 1][r],
+                                         up[r]);
                 else
                     v = q1[l - 1][r];
                 q0[l - 1][r] = q1[l - 1][r];
@@ -134,13 +144,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) tbc_pass_kernel(const T
             if (l == D && p >= z0 && p < z1) {
                 T *dp = dst + (long long)p * plane;
                 for (int r = 0; r < CPT; ++r)
-                    if (flags & (4u << (4 * r))) dp[goff[r]] = up[r];
+                    if ((flags & (4u << (4 * r))) && gok((long long)p * plane + goff[r])) dp[goff[r]] = up[r];
             }
         }
 #pragma unroll
         for (int l = 1; l < D; ++l)
             for (int r = 0; r < CPT; ++r)
-                if (flags & (8u << (4 * r))) lev[((l - 1) * 2 + (s & 1)) * WH + cell[r]] = q1[l][r];
+                if ((flags & (8u << (4 * r))) && sok(lev + ((l - 1) * 2 + (s & 1)) * WH + cell[r]))
+                    lev[((l - 1) * 2 + (s & 1)) * WH + cell[r]] = q1[l][r];
     }
     cp_async_wait_group<0>();
 }
@@ -169,6 +180,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) tbc4_pass_kernel(const 
     const int z0 = 1 + blockIdx.z * a.bz, z1 = min(z0 + a.bz, a.nz + 1);
     const float *__restrict__ src = static_cast<const float *>(a.src);
     float *__restrict__ dst = static_cast<float *>(a.dst);
+    // checked build: global offsets against the grid, shared indices against
+    // the ring and level planes
+    const long long SG = checked_grid_elems(a.nx, a.ny, a.nz, a.shrink);
+    const long long SS = (long long)(kRing + 2 * (D - 1)) * WH;
+    auto gok = [&](long long off) { return in_bounds(off, 1, SG, a.status); };
+    auto sok = [&](const float *ptr, int n) { return in_bounds(ptr - ring, n, SS, a.status); };
+    auto lds1 = [&](const float *ptr) { return sok(ptr, 1) ? *ptr : 0.f; };
 
     // flag bits of a quad: 0-3 load cell k, 4-7 cell k computes, 8-11 cell k
     // is stored, 12 owned, 13 has a left neighbour quad, 14 right, 15 row
@@ -202,7 +220,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) tbc4_pass_kernel(const 
         qc[r] = cy * W + 4 * qx;
         goff[r] = gy * (a.nx + 2) + x0 + 4 * qx;  // offset of cell 0 in a plane (used only for cells in the array)
     }
-    for (int c = tid; c < 2 * (D - 1) * WH; c += NT) lev[c] = 0.f;
+    for (int c = tid; c < 2 * (D - 1) * WH; c += NT)
+        if (sok(lev + c, 1)) lev[c] = 0.f;
 
     auto load_plane = [&](int p) {
         if (p >= 0 && p <= a.nz + 1) {
@@ -210,11 +229,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) tbc4_pass_kernel(const 
             const float *sp = src + (long long)p * plane;
             for (int r = 0; r < QPT; ++r)
                 for (int k = 0; k < 4; ++k)
-                    if (qf[r] & (1u << k)) cp_async_4(smem_addr(slot + qc[r] + k), sp + goff[r] + k);
+                    if ((qf[r] & (1u << k)) && sok(slot + qc[r] + k, 1) && gok((long long)p * plane + goff[r] + k))
+                        cp_async_4(smem_addr(slot + qc[r] + k), sp + goff[r] + k);
         }
         cp_async_commit();
     };
-    auto ld4 = [](const float *p) { return *reinterpret_cast<const float4 *>(p); };
+    auto ld4 = [&](const float *p) {
+        return sok(p, 4) ? *reinterpret_cast<const float4 *>(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
 
     const int s_begin = z0 - D + 1, s_end = z1 + D - 2;
     // q0[l][r]: level l (0 = input) at the plane below the one level l+1
@@ -252,8 +274,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) tbc4_pass_kernel(const 
                 const float4 c = ld4(nb + i0);  // level l-1 at plane p
                 float4 v = c;
                 if (zin && (f & kAny)) {
-                    const float w = (f & kLeft) ? nb[i0 - 1] : 0.f;
-                    const float e = (f & kRight) ? nb[i0 + 4] : 0.f;
+                    const float w = (f & kLeft) ? lds1(nb + i0 - 1) : 0.f;
+                    const float e = (f & kRight) ? lds1(nb + i0 + 4) : 0.f;
                     const float4 ym = (f & kUp) ? ld4(nb + i0 - W) : make_float4(0.f, 0.f, 0.f, 0.f);
                     const float4 yp = (f & kDown) ? ld4(nb + i0 + W) : make_float4(0.f, 0.f, 0.f, 0.f);
                     const float4 lo = q0[l - 1][r], hi = up[r];
@@ -281,16 +303,17 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) tbc4_pass_kernel(const 
                 q0[l - 1][r] = c;
                 up[r] = v;
                 // parity s&1 is read only in step s+1, after its barrier
-                if (l < D && (f & kOwned)) *reinterpret_cast<float4 *>(out + i0) = v;
+                if (l < D && (f & kOwned) && sok(out + i0, 4)) *reinterpret_cast<float4 *>(out + i0) = v;
             }
             if (l == D && p >= z0 && p < z1) {
                 float *dp = dst + (long long)p * plane;
                 for (int r = 0; r < QPT; ++r) {
                     const unsigned f = qf[r];
-                    if (f & 0x100u) dp[goff[r]] = up[r].x;
-                    if (f & 0x200u) dp[goff[r] + 1] = up[r].y;
-                    if (f & 0x400u) dp[goff[r] + 2] = up[r].z;
-                    if (f & 0x800u) dp[goff[r] + 3] = up[r].w;
+                    const long long go = (long long)p * plane + goff[r];
+                    if ((f & 0x100u) && gok(go)) dp[goff[r]] = up[r].x;
+                    if ((f & 0x200u) && gok(go + 1)) dp[goff[r] + 1] = up[r].y;
+                    if ((f & 0x400u) && gok(go + 2)) dp[goff[r] + 2] = up[r].z;
+                    if ((f & 0x800u) && gok(go + 3)) dp[goff[r] + 3] = up[r].w;
                 }
             }
         }

@@ -41,6 +41,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "checked.cuh"
 #include "jacobi_internal.h"
 #include "ptx.cuh"
 
@@ -111,6 +112,12 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
     const long long plane = (long long)P * (a.ny + 2);
     const float *__restrict__ src = static_cast<const float *>(a.src);
     float *__restrict__ dst = static_cast<float *>(a.dst);
+    // checked build: global offsets against the grid, ring indices against
+    // the ring, buffer indices against the level buffers
+    const long long SG = checked_grid_elems(a.nx, a.ny, a.nz, a.shrink);
+    auto gok = [&](long long off, int n) { return in_bounds(off, n, SG, a.status); };
+    auto rok = [&](const float *ptr, int n) { return in_bounds(ptr - ring, n, (long long)R * RING, a.status); };
+    auto bok = [&](const float *ptr) { return in_bounds(ptr - bufs, 4, 2LL * D * LEV, a.status); };
 
     // Per-cell masks (bit r*4+c): on the grid's interior (updated), in the
     // output tile (stored).
@@ -167,10 +174,14 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
             const uint32_t d0 = cp_dst0 + (uint32_t)((p & (R - 1)) * RING * 4);
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
+                const bool in = decltype(FAST)::value || ((cp_rows >> j) & 1u);
+                if (kChecked) {
+                    const float *dl = ring + (p & (R - 1)) * RING + cp_row * W + cp_col + j * RPJ * W;
+                    if (!rok(dl, A) || (in && !gok((long long)p * plane + cp_off0 + j * RPJ * P, A))) continue;
+                }
                 if (decltype(FAST)::value) {
                     tbr_copy<A>(d0 + (uint32_t)(j * RPJ * W * 4), sp + cp_off0 + j * RPJ * P, 4u * A);
                 } else {
-                    const bool in = (cp_rows >> j) & 1u;
                     tbr_copy<A>(d0 + (uint32_t)(j * RPJ * W * 4), in ? sp + cp_off0 + j * RPJ * P : sp,
                                 in ? 4u * A : 0u);
                 }
@@ -194,11 +205,14 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
         if ((rowfull >> r) & 1u) st_rest &= ~(0xFu << (r * 4));
 
     auto write_bounds = [&](float *b, const float (&v)[VY][4]) {
-        tbr_st4(b + o_top, v[0][0], v[0][1], v[0][2], v[0][3]);
-        tbr_st4(b + o_bot, v[VY - 1][0], v[VY - 1][1], v[VY - 1][2], v[VY - 1][3]);
-        tbr_st4(b + o_lcol, v[0][0], v[1][0], v[2][0], v[3][0]);
-        tbr_st4(b + o_rcol, v[0][3], v[1][3], v[2][3], v[3][3]);
+        if (bok(b + o_top)) tbr_st4(b + o_top, v[0][0], v[0][1], v[0][2], v[0][3]);
+        if (bok(b + o_bot)) tbr_st4(b + o_bot, v[VY - 1][0], v[VY - 1][1], v[VY - 1][2], v[VY - 1][3]);
+        if (bok(b + o_lcol)) tbr_st4(b + o_lcol, v[0][0], v[1][0], v[2][0], v[3][0]);
+        if (bok(b + o_rcol)) tbr_st4(b + o_rcol, v[0][3], v[1][3], v[2][3], v[3][3]);
     };
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto ldb = [&](const float *ptr) { return bok(ptr) ? tbr_ld4(ptr) : zero4; };
+    auto ldr = [&](const float *ptr) { return rok(ptr, 4) ? tbr_ld4(ptr) : zero4; };
 
     // z-queues: q[k][i] = level k (0 = input) at one of three consecutive
     // planes; at relative step t the new plane of every level goes to index
@@ -225,7 +239,7 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
         const float *r1 = ring_rd + (s_begin & (R - 1)) * RING;
 #pragma unroll
         for (int r = 0; r < VY; ++r) {
-            const float4 u = tbr_ld4(r0 + r * W), v = tbr_ld4(r1 + r * W);
+            const float4 u = ldr(r0 + r * W), v = ldr(r1 + r * W);
             q[0][2][r][0] = u.x, q[0][2][r][1] = u.y, q[0][2][r][2] = u.z, q[0][2][r][3] = u.w;
             q[0][0][r][0] = v.x, q[0][0][r][1] = v.y, q[0][0][r][2] = v.z, q[0][0][r][3] = v.w;
         }
@@ -247,7 +261,7 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
             const float *rp = ring_rd + ((s + 1) & (R - 1)) * RING;
 #pragma unroll
             for (int r = 0; r < VY; ++r) {
-                const float4 u = tbr_ld4(rp + r * W);
+                const float4 u = ldr(rp + r * W);
                 q[0][iN][r][0] = u.x, q[0][iN][r][1] = u.y, q[0][iN][r][2] = u.z, q[0][iN][r][3] = u.w;
             }
         }
@@ -257,8 +271,8 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
         // the shared-memory stores of the level in between (the compiler
         // cannot move loads across stores it cannot prove disjoint)
         float4 nbv[4];
-        nbv[0] = tbr_ld4(rb + o_above), nbv[1] = tbr_ld4(rb + o_below);
-        nbv[2] = tbr_ld4(rb + o_left), nbv[3] = tbr_ld4(rb + o_right);
+        nbv[0] = ldb(rb + o_above), nbv[1] = ldb(rb + o_below);
+        nbv[2] = ldb(rb + o_left), nbv[3] = ldb(rb + o_right);
         load_plane(s + R, FAST);  // into the slot of plane s, read in step t-1
         write_bounds(wb, q[0][iN]);
 #pragma unroll
@@ -269,8 +283,8 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
             const float4 above = nbv[0], below = nbv[1], left = nbv[2], right = nbv[3];
             if (l < D) {
                 const float *nn = rb + l * LEV;
-                nbv[0] = tbr_ld4(nn + o_above), nbv[1] = tbr_ld4(nn + o_below);
-                nbv[2] = tbr_ld4(nn + o_left), nbv[3] = tbr_ld4(nn + o_right);
+                nbv[0] = ldb(nn + o_above), nbv[1] = ldb(nn + o_below);
+                nbv[2] = ldb(nn + o_left), nbv[3] = ldb(nn + o_right);
             }
             // Cells (0,1) and (2,3) of a row form packed pairs.  The first
             // addition of Eq. (1) (x-neighbours) pairs cells unevenly and is
@@ -329,7 +343,8 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
                 if (A == 2) {
 #pragma unroll
                     for (int r = 0; r < VY; ++r) {
-                        const bool f = zst && ((rowfull >> r) & 1u);
+                        bool f = zst && ((rowfull >> r) & 1u);
+                        if (kChecked && f) f = gok((long long)p * plane + rowoff[r], 4);
                         tbr_st2_if(dp + rowoff[r], v[r][0], v[r][1], f);
                         tbr_st2_if(dp + rowoff[r] + 2, v[r][2], v[r][3], f);
                     }
@@ -339,7 +354,8 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
                     for (int r = 0; r < VY; ++r)
 #pragma unroll
                         for (int c = 0; c < 4; ++c)
-                            if ((st_rest >> (r * 4 + c)) & 1u) dp[rowoff[r] + c] = v[r][c];
+                            if (((st_rest >> (r * 4 + c)) & 1u) && gok((long long)p * plane + rowoff[r] + c, 1))
+                                dp[rowoff[r] + c] = v[r][c];
                 }
             }
         }

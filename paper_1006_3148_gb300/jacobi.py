@@ -70,6 +70,7 @@ def load(build_if_missing: bool = True):
             "jacobi_tune_candidates": ([P, pi, i], i),
             "jacobi_get_status": ([P, pi], i),
             "jacobi_debug_set_fault": ([P, i, i], i),
+            "jacobi_build_checked": ([], i),
             "jacobi_plan_passes": ([i, i, pi, i], i),
             "jacobi_profile_enable": ([P, i], i),
             "jacobi_poisson_residual": ([P, P, P, d, P, ctypes.POINTER(d)], i),

@@ -354,7 +354,7 @@ def run_reference(args, w):
 def _kernel_name(J, kernel: int, dtype: str) -> str:
     return {J.KERNEL_TB: "tb_pass_kernel", J.KERNEL_PLAIN: "plain_pass_kernel", J.KERNEL_PLAIN_X2: "plain_x2_kernel",
             J.KERNEL_TB_CTA: "tbc4_pass_kernel" if dtype == "f32" else "tbc_pass_kernel",
-            J.KERNEL_TB_REG: "tbr_pass_kernel"}[kernel]
+            J.KERNEL_TB_REG: "tbr_pass_kernel", J.KERNEL_TB_CHAIN: "tbx_pass_kernel"}[kernel]
 
 
 def run_ours(args, w, ctx, sub=False):
@@ -380,7 +380,7 @@ def run_ours(args, w, ctx, sub=False):
         ring = int(f[5]) if len(f) > 5 else 0
         threads = int(f[6]) if len(f) > 6 else 0
         J.jacobi_set_plan(h, {"tb": J.KERNEL_TB, "plain": J.KERNEL_PLAIN, "x2": J.KERNEL_PLAIN_X2,
-                              "cta": J.KERNEL_TB_CTA, "reg": J.KERNEL_TB_REG}[f[0]], int(f[1]), int(f[2]), int(f[3]), int(f[4]), ring, threads)
+                              "cta": J.KERNEL_TB_CTA, "reg": J.KERNEL_TB_REG, "chain": J.KERNEL_TB_CHAIN}[f[0]], int(f[1]), int(f[2]), int(f[3]), int(f[4]), ring, threads)
     elif not args.no_tune:
         sa, sb = torch.empty_like(A), torch.empty_like(A)
         tune_glups = J.jacobi_tune(h, sa, sb)
@@ -731,7 +731,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fp64_512", choices=sorted(WORKLOADS))
     ap.add_argument("--plan", default=None, help="force a plan kernel:depth:bx:by:bz[:ring[:threads]], kernel tb, cta, "
-                    "reg, plain or x2, e.g. tb:4:64:16:64:8, cta:4:64:32:64:0:512 or x2:1:32:8:16")
+                    "reg, chain (ring = CTAs), plain or x2, e.g. tb:4:64:16:64:8, cta:4:64:32:64:0:512 or x2:1:32:8:16")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -69,11 +69,18 @@ enum {
     JACOBI_KERNEL_TB_CTA = 4, /* temporal blocking inside one CTA: depth 1..4
                                 levels applied to a tile's planes in shared
                                 memory (T updates per thread, Sect. 2.1)     */
-    JACOBI_KERNEL_TB_REG = 5 /* temporal blocking inside one CTA with
+    JACOBI_KERNEL_TB_REG = 5, /* temporal blocking inside one CTA with
                                 register-blocked cells (FP32 only): every
                                 thread keeps a 4 x 4 cell block of each level
                                 in registers and exchanges only its block
                                 boundary through shared memory; depth 1..4  */
+    JACOBI_KERNEL_TB_CHAIN = 6 /* temporal blocking by a chain of 2..4 CTAs
+                                of a thread-block cluster (FP32 only), each
+                                applying up to 4 levels of the register-
+                                blocked step and handing its last level to
+                                the next CTA through distributed shared
+                                memory: depth up to 16 per pass (the team
+                                of threads x T updates of Sect. 2.1)      */
 };
 
 typedef struct jacobi_plan_s *jacobi_h;
@@ -131,13 +138,18 @@ int jacobi_sweep_host(jacobi_h h, const void *A_host, void *out_host, int T,
  * side -- one of 64x32, 64x64 or 128x32 (threads = bx*by/16, each owning
  * 4 x 4 cells), depth 1..4, z chunk bz; the output tile is (bx - 2 depth,
  * rounded down to even when nx is even) x (by - 2 depth); ring and threads
- * ignored.  For PLAIN and PLAIN_X2:
+ * ignored.  For TB_CHAIN (FP32 grids only): depth d = total levels per pass,
+ * ring = c, the CTAs of the chain (2..4, c <= d <= 4c; levels are split as
+ * evenly as possible, d/c rounded up per CTA at most), bx*by = region, 64x32
+ * (d <= 15) or 64x64, as for TB_REG at depth d, z chunk bz; threads ignored.
+ * Passes of depth below c run on the one-CTA TB_REG kernel.  For PLAIN and
+ * PLAIN_X2:
  * bx*by = CTA shape in threads (bx a multiple of 32, bx*by <= 1024; a
  * PLAIN_X2 thread covers two x cells) and bz = planes each thread walks in
  * z; ring and threads are ignored.  A zero bx, by or bz takes the family's
  * default (PLAIN 32 x 8 x 8; PLAIN_X2 32 x 8 x 16; TB 64 x 16 x 64; TB_CTA
- * 64 x 32 x 64; TB_REG region 64 x 32, 64 planes; tiles clamped to the
- * grid).  JACOBI_KERNEL_AUTO returns to
+ * 64 x 32 x 64; TB_REG region 64 x 32, 64 planes; TB_CHAIN region
+ * 64 x 64, 64 planes, 2 CTAs; tiles clamped to the grid).  JACOBI_KERNEL_AUTO returns to
  * the tuned/default plan.  Returns JACOBI_ERR_ARG for out-of-range fields and JACOBI_ERR_UNSUPPORTED
  * if the plan cannot launch on this device (shared memory, registers,
  * cluster occupancy). */
@@ -216,7 +228,8 @@ int jacobi_profile_enable(jacobi_h h, int enable);
 int jacobi_profile_read(jacobi_h h, double *pass_ms, int *pass_launches, int *other_launches);
 
 /* Test hook for failure detection: mode 1 makes the next pass kernel omit
- * one mbarrier arrival so that its bounded waits run out (after
+ * one mbarrier arrival (TB: a cp.async arrival; TB_CHAIN: the first CTA's
+ * hand-off of one plane) so that its bounded waits run out (after
  * limit_ms milliseconds); the kernel records JACOBI_ERR_TIMEOUT and returns
  * without faulting.  Mode 2 (bounds-checked build only, else
  * JACOBI_ERR_UNSUPPORTED): the kernels check their accesses against grids

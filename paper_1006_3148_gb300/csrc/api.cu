@@ -95,11 +95,13 @@ bool prof_event(jacobi_plan_s *h, cudaStream_t s)
 Plan resolve_plan(const jacobi_plan_s *h, Plan p)
 {
     const bool plain = p.kernel == JACOBI_KERNEL_PLAIN || p.kernel == JACOBI_KERNEL_PLAIN_X2;
-    if (p.kernel == JACOBI_KERNEL_TB_REG) {
+    if (p.kernel == JACOBI_KERNEL_TB_REG || p.kernel == JACOBI_KERNEL_TB_CHAIN) {
+        const bool chain = p.kernel == JACOBI_KERNEL_TB_CHAIN;
         if (p.bx == 0) p.bx = 64;
-        if (p.by == 0) p.by = 32;
+        if (p.by == 0) p.by = chain ? 64 : 32;
         if (p.bz == 0) p.bz = std::min(64, h->nz);
-        p.ring = 0;
+        if (!chain) p.ring = 0;
+        else if (p.ring == 0) p.ring = 2;
         p.threads = p.bx * p.by / 16;
         return p;
     }
@@ -120,6 +122,32 @@ int check_plan(const jacobi_plan_s *h, const Plan &p)
         // (row block, z chunk) pairs must fit grid y * grid z
         const long long pairs = (long long)((h->ny + p.by - 1) / p.by) * ((h->nz + p.bz - 1) / p.bz);
         return pairs <= 65535ll * 65535ll ? JACOBI_OK : JACOBI_ERR_UNSUPPORTED;
+    }
+    if (p.kernel == JACOBI_KERNEL_TB_CHAIN) {
+        if (p.depth < 2 || p.depth > 16 || p.bz < 1 || p.ring < 2 || p.ring > 4) return JACOBI_ERR_ARG;
+        TbxArgs a;
+        a.nx = h->nx;
+        a.ny = h->ny;
+        a.nz = h->nz;
+        a.bz = p.bz;
+        size_t smem = 0;
+        const int st = tbx_configure(p.depth, p.ring, p.bx, p.by, &a, &smem);
+        if (st != JACOBI_OK) return st;
+        if (h->dtype != JACOBI_F32) return JACOBI_ERR_UNSUPPORTED;
+        int clusters = 0;
+        if (tbx_max_clusters(p.depth, p.ring, p.bx, p.by, h->nx, &clusters) != cudaSuccess) {
+            cudaGetLastError();
+            return JACOBI_ERR_UNSUPPORTED;
+        }
+        // passes of depth below the chain length run on the one-CTA kernel
+        TbrArgs b;
+        b.nx = h->nx;
+        b.ny = h->ny;
+        b.nz = h->nz;
+        b.bz = p.bz;
+        for (int d = 1; d < p.ring; ++d)
+            if (tbr_configure(d, p.bx, p.by, &b, &smem, nullptr) != JACOBI_OK) return JACOBI_ERR_UNSUPPORTED;
+        return clusters > 0 ? JACOBI_OK : JACOBI_ERR_UNSUPPORTED;
     }
     if (p.kernel == JACOBI_KERNEL_TB_REG) {
         if (p.depth < 1 || p.depth > 4 || p.bz < 1) return JACOBI_ERR_ARG;
@@ -192,7 +220,8 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
     std::vector<int> depths((size_t)T + 1);
     const int P = plan_passes(T, p.depth, depths.data(), T + 1);
     if (P < 0) return JACOBI_ERR_ARG;
-    if (p.kernel == JACOBI_KERNEL_TB_REG) {
+    if (p.kernel == JACOBI_KERNEL_TB_REG || p.kernel == JACOBI_KERNEL_TB_CHAIN) {
+        const bool chain = p.kernel == JACOBI_KERNEL_TB_CHAIN;
         TbrArgs a;
         a.nx = h->nx;
         a.ny = h->ny;
@@ -200,11 +229,25 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
         a.bz = p.bz;
         a.status = h->d_status;
         a.shrink = h->check_shrink;
+        TbxArgs c;
+        c.nx = h->nx;
+        c.ny = h->ny;
+        c.nz = h->nz;
+        c.bz = p.bz;
+        c.status = h->d_status;
+        c.shrink = h->check_shrink;
+        c.limit_ns = h->limit_ns;
         for (int q = 0; q < P; ++q) {
             if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
-            a.src = (q % 2 == 0) ? A : B;
-            a.dst = (q % 2 == 0) ? B : A;
-            e = tbr_launch(depths[q], p.bx, p.by, a, s);
+            a.src = c.src = (q % 2 == 0) ? A : B;
+            a.dst = c.dst = (q % 2 == 0) ? B : A;
+            if (chain && depths[q] >= p.ring) {
+                c.fault_mode = h->fault_mode;
+                h->fault_mode = 0;
+                e = tbx_launch(depths[q], p.ring, p.bx, p.by, c, s);
+            } else {
+                e = tbr_launch(depths[q], p.bx, p.by, a, s);
+            }
             if (e != cudaSuccess) return cuda_fail(e);
             if (!prof_event(h, s)) return JACOBI_ERR_CUDA;
             if (h->prof) ++h->prof_pass;
@@ -570,6 +613,20 @@ std::vector<Plan> tune_candidates(const jacobi_plan_s *h)
                     p.threads = r[0] * r[1] / 16;
                     out.push_back(p);
                 }
+        // chains of CTAs: (depth, CTAs) x region, z chunk 128
+        const int chains[][2] = {{4, 2}, {6, 2}, {6, 3}, {8, 2}, {8, 4}};
+        for (const auto &c : chains)
+            for (int by : {32, 64}) {
+                Plan p;
+                p.kernel = JACOBI_KERNEL_TB_CHAIN;
+                p.depth = c[0];
+                p.ring = c[1];
+                p.bx = 64;
+                p.by = by;
+                p.bz = std::min(128, h->nz);
+                p.threads = 64 * by / 16;
+                out.push_back(p);
+            }
     }
     const int depths64[] = {1, 2, 4};
     const int depths32[] = {1, 2, 4, 6, 8};

@@ -53,6 +53,24 @@ struct TbrArgs {
     long long shrink = 0;
 };
 
+// Arguments of one pass of the chained-cluster kernel (FP32): a cluster of
+// `cluster` CTAs per tile, CTA r applying levels[r] of the pass's `depth`
+// time levels (lev_before[r] = levels of CTAs 0..r-1); tile geometry as for
+// the one-CTA register-blocked kernel at that depth.
+struct TbxArgs {
+    const void *src;
+    void *dst;
+    int nx, ny, nz;
+    int bx, by, bz;
+    int x_first, off;
+    int depth, cluster;
+    int levels[4], lev_before[4];
+    int *status = nullptr;
+    unsigned long long limit_ns = 2000000000ull;
+    int fault_mode = 0;  // test hook: 1 = CTA 0 never hands over its third plane
+    long long shrink = 0;
+};
+
 struct PlainArgs {
     const void *src;
     void *dst;
@@ -102,6 +120,12 @@ cudaError_t plain_launch(int dtype, PlainArgs a, cudaStream_t s);
 int tbc_configure(int dtype, int depth, int bx, int by, int threads, TbcArgs *a, size_t *smem);
 cudaError_t tbc_launch(int dtype, int depth, int threads, const TbcArgs &a, cudaStream_t s);
 cudaError_t plain_x2_launch(int dtype, PlainArgs a, cudaStream_t s);  // nx even
+// Chained-cluster temporal blocking (FP32): `cluster` (2..4) CTAs of a
+// thread-block cluster, `depth` (>= cluster, <= 4 * cluster) levels split as
+// evenly as possible; region W x H in {64x32, 64x64}.  Fills a; launches one pass.
+int tbx_configure(int depth, int cluster, int W, int H, TbxArgs *a, size_t *smem);
+cudaError_t tbx_launch(int depth, int cluster, int W, int H, const TbxArgs &a, cudaStream_t s);
+cudaError_t tbx_max_clusters(int depth, int cluster, int W, int H, int nx, int *clusters);
 // Register-blocked one-CTA temporal blocking (FP32): region W x H (W in
 // {64, 128}, H in {32, 64}; 16 cells per thread), depth 1..4.  Checks the
 // plan and fills the tile fields of a; launches one pass.

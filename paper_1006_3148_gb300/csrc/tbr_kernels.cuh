@@ -81,6 +81,48 @@ __device__ __forceinline__ void tbr_st4(float *p, float a, float b, float c, flo
     *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
 }
 
+// One time level of Eq. (1) on a thread's 4 x 4 block of cells: cur, below
+// and above hold the previous level at the plane updated and at the planes
+// below and above it (own cells); the row above the block, the row below,
+// the column left and the column right come from the neighbouring blocks.
+// Cells (0,1) and (2,3) of a row form packed pairs: the first addition
+// (the x-neighbours) pairs cells unevenly and is done per cell, straight
+// into a pair; the other four additions and the multiplication by RN(1/6)
+// run on pairs.  Every cell keeps the left-to-right order of Eq. (1).
+__device__ __forceinline__ void tbr_block_update(const float (&cur)[kTbrVY][4], const float (&below_pl)[kTbrVY][4],
+                                                 const float (&above_pl)[kTbrVY][4], float4 above, float4 below,
+                                                 float4 left, float4 right, float (&v)[kTbrVY][4])
+{
+    constexpr int VY = kTbrVY;
+    const float sixth = 1.0f / 6.0f;
+    const float le[4] = {left.x, left.y, left.z, left.w};
+    const float ri[4] = {right.x, right.y, right.z, right.w};
+    const float2 ab0 = make_float2(above.x, above.y), ab1 = make_float2(above.z, above.w);
+    const float2 be0 = make_float2(below.x, below.y), be1 = make_float2(below.z, below.w);
+    const float2 six2 = make_float2(sixth, sixth);
+#pragma unroll
+    for (int r = 0; r < VY; ++r) {
+        const float c0 = cur[r][0], c1 = cur[r][1], c2 = cur[r][2], c3 = cur[r][3];
+        float2 lo = make_float2(__fadd_rn(le[r], c1), __fadd_rn(c0, c2));
+        float2 hi = make_float2(__fadd_rn(c1, c3), __fadd_rn(c2, ri[r]));
+        const float2 s0 = r > 0 ? make_float2(cur[r - 1][0], cur[r - 1][1]) : ab0;
+        const float2 s1 = r > 0 ? make_float2(cur[r - 1][2], cur[r - 1][3]) : ab1;
+        const float2 n0 = r < VY - 1 ? make_float2(cur[r + 1][0], cur[r + 1][1]) : be0;
+        const float2 n1 = r < VY - 1 ? make_float2(cur[r + 1][2], cur[r + 1][3]) : be1;
+        lo = __fadd2_rn(lo, s0);
+        hi = __fadd2_rn(hi, s1);
+        lo = __fadd2_rn(lo, n0);
+        hi = __fadd2_rn(hi, n1);
+        lo = __fadd2_rn(lo, make_float2(below_pl[r][0], below_pl[r][1]));
+        hi = __fadd2_rn(hi, make_float2(below_pl[r][2], below_pl[r][3]));
+        lo = __fadd2_rn(lo, make_float2(above_pl[r][0], above_pl[r][1]));
+        hi = __fadd2_rn(hi, make_float2(above_pl[r][2], above_pl[r][3]));
+        lo = __fmul2_rn(lo, six2);
+        hi = __fmul2_rn(hi, six2);
+        v[r][0] = lo.x, v[r][1] = lo.y, v[r][2] = hi.x, v[r][3] = hi.y;
+    }
+}
+
 // Resident CTAs requested per SM: three 128-thread CTAs at depth <= 2 (at
 // most 170 registers, which those depths fit without spilling), else one.
 template <int D, int NT>
@@ -249,7 +291,6 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
 #pragma unroll
     for (int i = 1; i < R; ++i) load_plane(s_begin + i, slow_c);
 
-    const float sixth = 1.0f / 6.0f;
     auto step = [&](auto J, auto FAST, int t) {
         constexpr int j = decltype(J)::value;
         constexpr bool fast = decltype(FAST)::value;
@@ -286,37 +327,8 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
                 nbv[0] = ldb(nn + o_above), nbv[1] = ldb(nn + o_below);
                 nbv[2] = ldb(nn + o_left), nbv[3] = ldb(nn + o_right);
             }
-            // Cells (0,1) and (2,3) of a row form packed pairs.  The first
-            // addition of Eq. (1) (x-neighbours) pairs cells unevenly and is
-            // done per cell, straight into a pair; the other four additions
-            // and the multiplication run on pairs (same per-cell rounding).
-            const float le[4] = {left.x, left.y, left.z, left.w};
-            const float ri[4] = {right.x, right.y, right.z, right.w};
-            const float2 ab0 = make_float2(above.x, above.y), ab1 = make_float2(above.z, above.w);
-            const float2 be0 = make_float2(below.x, below.y), be1 = make_float2(below.z, below.w);
-            const float2 six2 = make_float2(sixth, sixth);
             float v[VY][4];
-#pragma unroll
-            for (int r = 0; r < VY; ++r) {
-                const float c0 = q[k][iC][r][0], c1 = q[k][iC][r][1], c2 = q[k][iC][r][2], c3 = q[k][iC][r][3];
-                float2 lo = make_float2(__fadd_rn(le[r], c1), __fadd_rn(c0, c2));
-                float2 hi = make_float2(__fadd_rn(c1, c3), __fadd_rn(c2, ri[r]));
-                const float2 s0 = r > 0 ? make_float2(q[k][iC][r - 1][0], q[k][iC][r - 1][1]) : ab0;
-                const float2 s1 = r > 0 ? make_float2(q[k][iC][r - 1][2], q[k][iC][r - 1][3]) : ab1;
-                const float2 n0 = r < VY - 1 ? make_float2(q[k][iC][r + 1][0], q[k][iC][r + 1][1]) : be0;
-                const float2 n1 = r < VY - 1 ? make_float2(q[k][iC][r + 1][2], q[k][iC][r + 1][3]) : be1;
-                lo = __fadd2_rn(lo, s0);
-                hi = __fadd2_rn(hi, s1);
-                lo = __fadd2_rn(lo, n0);
-                hi = __fadd2_rn(hi, n1);
-                lo = __fadd2_rn(lo, make_float2(q[k][iM][r][0], q[k][iM][r][1]));
-                hi = __fadd2_rn(hi, make_float2(q[k][iM][r][2], q[k][iM][r][3]));
-                lo = __fadd2_rn(lo, make_float2(q[k][iN][r][0], q[k][iN][r][1]));
-                hi = __fadd2_rn(hi, make_float2(q[k][iN][r][2], q[k][iN][r][3]));
-                lo = __fmul2_rn(lo, six2);
-                hi = __fmul2_rn(hi, six2);
-                v[r][0] = lo.x, v[r][1] = lo.y, v[r][2] = hi.x, v[r][3] = hi.y;
-            }
+            tbr_block_update(q[k][iC], q[k][iM], q[k][iN], above, below, left, right, v);
             if (fast) {
                 if (!zin) {  // uniform: a halo plane (or one outside the array)
 #pragma unroll

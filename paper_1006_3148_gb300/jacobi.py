@@ -17,7 +17,7 @@ from . import build as _build
 
 F64 = 0
 F32 = 1
-KERNEL_AUTO, KERNEL_PLAIN, KERNEL_TB, KERNEL_PLAIN_X2, KERNEL_TB_CTA, KERNEL_TB_REG = 0, 1, 2, 3, 4, 5
+KERNEL_AUTO, KERNEL_PLAIN, KERNEL_TB, KERNEL_PLAIN_X2, KERNEL_TB_CTA, KERNEL_TB_REG, KERNEL_TB_CHAIN = 0, 1, 2, 3, 4, 5, 6
 BATCH_PERSISTENT, BATCH_SWEEPS = 0, 1
 
 STATUS = {

@@ -51,3 +51,22 @@ def test_512cubed_fp64_bit_exact(c2, plan):
     got = _run(A0, plan)
     bad = np.flatnonzero(got != exp)
     assert bad.size == 0, "first mismatch at flat index %d: %r vs %r" % (bad[0], got.flat[bad[0]], exp.flat[bad[0]])
+
+
+def test_512cubed_fp32_chain_bitwise():
+    # the same recipe in FP32 through a chain of 2 CTAs of 4 levels each
+    # (depth 8 per pass), compared bitwise with the oracle's FP32 loop
+    A0 = inputs.dirichlet_z0_grid(N, N, N, seed=2).to(torch.float32)
+    exp = oracle.jacobi_result(A0.numpy(), T)
+    h = J.Handle(N, N, N, torch.float32)
+    J.jacobi_set_plan(h, J.KERNEL_TB_CHAIN, 8, 64, 64, 128, 2)
+    A = A0.cuda()
+    B = torch.empty_like(A)
+    out = J.jacobi_sweep(h, A, B, T)
+    torch.cuda.synchronize()
+    assert J.jacobi_get_status(h) == 0
+    got = out.cpu().numpy()
+    del A, B, out
+    torch.cuda.empty_cache()
+    bad = np.flatnonzero(got != exp)
+    assert bad.size == 0, bad.size

@@ -84,9 +84,9 @@ def _check(shape, seed, dtype, T, plan):
 RAGGED = [(150, 70, 45), (66, 37, 29)]
 
 
-FAMILIES = [J.KERNEL_PLAIN, J.KERNEL_PLAIN_X2, J.KERNEL_TB_CTA, J.KERNEL_TB, J.KERNEL_TB_REG]
-FAMILY_IDS = ["plain", "x2", "cta", "tb", "reg"]
-FAMILIES64 = FAMILIES[:4]  # the register-blocked family is FP32 only
+FAMILIES = [J.KERNEL_PLAIN, J.KERNEL_PLAIN_X2, J.KERNEL_TB_CTA, J.KERNEL_TB, J.KERNEL_TB_REG, J.KERNEL_TB_CHAIN]
+FAMILY_IDS = ["plain", "x2", "cta", "tb", "reg", "chain"]
+FAMILIES64 = FAMILIES[:4]  # the register-blocked families are FP32 only
 
 
 # The candidate lists are read inside the tests (they need the GPU), one

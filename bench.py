@@ -560,11 +560,21 @@ def run_batch(args, w, ctx, sub=False):
         torch.cuda.empty_cache()
     info = J.jacobi_batch_get_info(b)
     eng = J.jacobi_batch_get_engine(b)
+    depth32 = J.jacobi_batch_get_fp32_depth(b)
     sweeps_engine = eng["engine"] == J.BATCH_SWEEPS
     launches_per_run = (1 + T) if sweeps_engine else 2
+    passes32 = T
+    if depth32 > 1:
+        # FP32 grids in blocked passes: one launch per pass and row-pitch parity
+        passes32 = len(J.jacobi_plan_passes(T, depth32))
+        pitches = {(nx + 2) % 2 for (nx, ny, nz), f in zip(dims, f32) if f}
+        launches_per_run += passes32 * len(pitches)
     lups = float(sum(nx * ny * nz for nx, ny, nz in dims)) * T
     lups64 = float(sum(nx * ny * nz for (nx, ny, nz), f in zip(dims, f32) if not f)) * T
-    bytes_alg = float(sum(2 * (4 if f else 8) * nx * ny * nz for (nx, ny, nz), f in zip(dims, f32))) * T
+    # algorithmic bytes: read and write each cell once per sweep (FP64, and
+    # FP32 at depth 1) or once per blocked pass (FP32 at depth > 1)
+    bytes_alg = float(sum(2 * 8 * nx * ny * nz for (nx, ny, nz), f in zip(dims, f32) if not f)) * T + \
+        float(sum(2 * 4 * nx * ny * nz for (nx, ny, nz), f in zip(dims, f32) if f)) * passes32
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
@@ -600,7 +610,7 @@ def run_batch(args, w, ctx, sub=False):
         roof = {"bound": "hbm", "achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
                 "traffic": None, "peak_source": peak_src}
     roof["kernel"] = "batch_sweep_kernel" if sweeps_engine else "batch_kernel"
-    if sweeps_engine and BATCH_SWEEP_TRAFFIC is not None:
+    if sweeps_engine and depth32 == 1 and BATCH_SWEEP_TRAFFIC is not None:
         # DRAM bytes per LUP of one sweep launch over the batch (ncu capture)
         roof["traffic"] = BATCH_SWEEP_TRAFFIC[0] * lups / T
         roof["traffic_source"] = BATCH_SWEEP_TRAFFIC[1]
@@ -611,7 +621,7 @@ def run_batch(args, w, ctx, sub=False):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": batch_config(w, ws),
-        "plan": {"engine": "sweeps" if sweeps_engine else "persistent",
+        "plan": {"engine": "sweeps" if sweeps_engine else "persistent", "fp32_depth": depth32,
                  **({"planes_per_thread": eng["kz"]} if sweeps_engine else
                     {"tile": [info["bx"], info["by"], info["bz"]], "items": info["items"],
                      "persistent_ctas": info["blocks"]})},

@@ -358,10 +358,25 @@ int jacobi_batch_set_engine(jacobi_batch_h b, int engine, int kz);
 /* Current engine and sweep-engine planes per thread (either may be NULL). */
 int jacobi_batch_get_engine(jacobi_batch_h b, int *engine, int *kz);
 
+/* Temporal depth of the batch's FP32 grids (Sect. 2.1 and 3.1): depth 1
+ * (initially) sweeps them with the selected engine like the FP64 grids;
+ * depth 2..4 takes them out of that engine and sweeps each FP32 grid g in
+ * passes of depth <= depth (the pass count has the parity of T_g, so the
+ * result buffer is unchanged) by the register-blocked one-CTA kernel of
+ * JACOBI_KERNEL_TB_REG with 64 x 32 regions and z chunks of 128 planes, all
+ * FP32 grids of one pass in one launch, on a branch of the graph that runs
+ * beside the FP64 grids' launches.  Results stay bit-identical to depth 1.
+ * Such grids take no source term: jacobi_batch_run_rhs returns
+ * JACOBI_ERR_UNSUPPORTED if RHS[g] is non-NULL for one of them.
+ * Re-captures the graph; JACOBI_ERR_ARG for a depth outside 1..4. */
+int jacobi_batch_set_fp32_depth(jacobi_batch_h b, int depth);
+int jacobi_batch_get_fp32_depth(jacobi_batch_h b, int *depth);
+
 /* Autotuner for the batch: fills the caller's scratch grids (arrays of n
  * device pointers, same shapes as the batch) with a constant, times the
- * sweep engine at several planes per thread and the persistent engine at
- * several tiles, and keeps the fastest.  Synchronises stream. */
+ * sweep engine at several planes per thread, the persistent engine at
+ * several tiles and, where the batch has FP32 grids, FP32 depths 2 and 3,
+ * and keeps the fastest.  Synchronises stream. */
 int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scratchB,
                       jacobi_stream_t stream, double *glups);
 

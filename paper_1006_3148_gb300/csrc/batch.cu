@@ -12,6 +12,10 @@
 // Persistent engine (JACOBI_BATCH_PERSISTENT): all T_g sweeps of all grids
 // in ONE persistent launch.
 //
+// FP32 depth d > 1 (jacobi_batch_set_fp32_depth): the FP32 grids leave both
+// engines and are swept by temporally blocked passes of depth <= d
+// (batch_tbr.cu), on a branch of the graph that runs beside the FP64 work.
+//
 // Work items are (grid g, tile t of g, sweep p), numbered pass-major:
 // item = p * total_tiles + (tile_base[g] + t).  Resident CTAs take items
 // from a global atomic counter, so items are started in that order.  Item
@@ -33,22 +37,13 @@
 #include <vector>
 
 #include "arith.cuh"
+#include "batch_internal.h"
 #include "checked.cuh"
 #include "grid.cuh"
 #include "jacobi_internal.h"
 #include "ptx.cuh"
 
 namespace jac {
-
-struct BatchGrid {
-    void *A;
-    void *B;
-    const void *rhs;  // optional source term g (same dtype): update (sum + g)/6
-    int nx, ny, nz, dtype, T;
-    int ntx, nty, ntz;
-    int tile_base;  // global index of this grid's tile 0
-    int nbxy, nbz;  // sweep engine: runs of kSweepThreads x-y cells, z chunks
-};
 
 // Sweep engine: grid g's units are numbered from unit_base within the list
 // of grids of its dtype (FP64 list first in the table, then FP32).
@@ -163,7 +158,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs a)
         const BatchGrid G = a.grids[lo];
         const int t = tg - G.tile_base, txy = G.ntx * G.nty;
         const int tx = t % G.ntx, ty = (t / G.ntx) % G.nty, tz = t / txy;
-        if (p >= G.T) continue;  // this grid is done; nothing waits on it
+        if (p >= G.Te) continue;  // this grid is done; nothing waits on it
         if (threadIdx.x == 0) {
             bool ok = true;
             if (p > 0) {
@@ -261,7 +256,7 @@ __global__ void __launch_bounds__(kSweepThreads) batch_sweep_kernel(const BatchG
         else hi = mid - 1;
     }
     const BatchGrid &G = grids[t[lo].grid];
-    if (p >= G.T) return;
+    if (p >= G.Te) return;
     const int u = (int)(idx - t[lo].unit_base);
     // element type and source term are uniform per block: the plane loop is
     // instantiated for each combination
@@ -301,6 +296,9 @@ struct jacobi_batch_s {
     int engine = JACOBI_BATCH_SWEEPS;
     int kz = 16;                   // sweep engine: planes per thread
     SweepEntry *d_tab = nullptr;   // sweep engine: FP64 list, then FP32 list
+    int fp32_depth = 1;            // > 1: FP32 grids by blocked passes
+    TbrBatchEntry *d_tbr = nullptr;
+    std::vector<TbrBatchLaunch> tbr_launches;
     int n64 = 0, n32 = 0;
     long long u64 = 0, u32 = 0;    // units per list
     int bx = 32, by = 8, bz = 0;  // bz 0: whole z column per item
@@ -321,23 +319,31 @@ namespace {
 
 thread_local std::string g_batch_err;
 
+// Whether grid G is swept by the sweep or persistent engine.
+bool engine_grid(const jacobi_batch_s *b, const BatchGrid &G)
+{
+    return G.dtype == JACOBI_F64 || b->fp32_depth == 1;
+}
+
 void layout(jacobi_batch_s *b)
 {
     int base = 0;
     b->max_T = 0;
     for (BatchGrid &G : b->grids) {
+        G.Te = engine_grid(b, G) ? G.T : 0;
         G.ntx = (G.nx + b->bx - 1) / b->bx;
         G.nty = (G.ny + b->by - 1) / b->by;
         G.ntz = (b->bz > 0) ? (G.nz + b->bz - 1) / b->bz : 1;
         G.tile_base = base;
         base += G.ntx * G.nty * G.ntz;
-        b->max_T = std::max(b->max_T, G.T);
+        b->max_T = std::max(b->max_T, G.Te);
     }
     b->total_tiles = base;
     b->total_items = (long long)base * b->max_T;
     b->n64 = b->n32 = 0;
     b->u64 = b->u32 = 0;
     for (BatchGrid &G : b->grids) {
+        if (!engine_grid(b, G)) continue;
         G.nbxy = (G.nx * G.ny + kSweepThreads - 1) / kSweepThreads;
         G.nbz = (G.nz + b->kz - 1) / b->kz;
         const long long units = (long long)G.nbxy * G.nbz;
@@ -361,7 +367,7 @@ std::vector<SweepEntry> sweep_table(const jacobi_batch_s *b)
         long long base = 0;
         for (int g = 0; g < b->n; ++g) {
             const BatchGrid &G = b->grids[(size_t)g];
-            if ((G.dtype == JACOBI_F64) != (pass == 0)) continue;
+            if ((G.dtype == JACOBI_F64) != (pass == 0) || !engine_grid(b, G)) continue;
             t.push_back(SweepEntry{base, g});
             base += (long long)G.nbxy * G.nbz;
         }
@@ -378,8 +384,9 @@ void free_graph(jacobi_batch_s *b)
 }
 
 // (Re)allocates the control block for the current layout and captures the
-// graph: reset of the item counter and progress counters, the halo copy of
-// every grid, and the persistent launch.
+// graph: (persistent engine) reset of the item counter and progress
+// counters, the halo copy of every grid, then the engine's launches and,
+// for an FP32 depth above 1, the blocked FP32 passes on a second branch.
 int build_graph(jacobi_batch_s *b)
 {
     free_graph(b);
@@ -415,33 +422,70 @@ int build_graph(jacobi_batch_s *b)
         const std::vector<SweepEntry> tab = sweep_table(b);
         if (b->d_tab) cudaFree(b->d_tab);
         b->d_tab = nullptr;
-        e = cudaMalloc(&b->d_tab, sizeof(SweepEntry) * (size_t)b->n);
+        e = cudaMalloc(&b->d_tab, sizeof(SweepEntry) * std::max<size_t>(1, tab.size()));
         if (e != cudaSuccess) return JACOBI_ERR_ALLOC;
-        e = cudaMemcpy(b->d_tab, tab.data(), sizeof(SweepEntry) * (size_t)b->n, cudaMemcpyHostToDevice);
+        if (!tab.empty())
+            e = cudaMemcpy(b->d_tab, tab.data(), sizeof(SweepEntry) * tab.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return JACOBI_ERR_CUDA;
     }
+    std::vector<TbrBatchEntry> ttab;
+    b->tbr_launches.clear();
+    if (b->fp32_depth > 1) batch_tbr_plan(b->grids, b->fp32_depth, ttab, b->tbr_launches);
+    if (b->d_tbr) cudaFree(b->d_tbr);
+    b->d_tbr = nullptr;
+    if (!ttab.empty()) {
+        e = cudaMalloc(&b->d_tbr, sizeof(TbrBatchEntry) * ttab.size());
+        if (e != cudaSuccess) return JACOBI_ERR_ALLOC;
+        e = cudaMemcpy(b->d_tbr, ttab.data(), sizeof(TbrBatchEntry) * ttab.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return JACOBI_ERR_CUDA;
+    }
+    for (const TbrBatchLaunch &L : b->tbr_launches)
+        if (batch_tbr_configure(L) != cudaSuccess) return JACOBI_ERR_CUDA;
     const long long units = b->u64 + b->u32;
-    const unsigned gx = (unsigned)std::min<long long>(units, 1ll << 30);
+    const unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>(units, 1ll << 30));
     const unsigned gy = (unsigned)((units + gx - 1) / gx);
-    cudaStream_t cs;
+    cudaStream_t cs, cs2;
+    cudaEvent_t fork, join;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return JACOBI_ERR_CUDA;
+    e = cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return JACOBI_ERR_CUDA;
+    }
+    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    const bool branch = !b->tbr_launches.empty();
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+        if (b->engine == JACOBI_BATCH_PERSISTENT) {
+            cudaMemsetAsync(b->d_ctl, 0, sizeof(int), cs);
+            cudaMemsetAsync(b->d_ctl + 2, 0, sizeof(int) * (size_t)b->total_tiles, cs);
+        }
+        batch_halo_kernel<<<dim3(64, (unsigned)b->n), 256, 0, cs>>>(b->d_grids, a.status, a.shrink);
+        cudaError_t eb = cudaSuccess;
+        if (branch) {
+            eb = cudaEventRecord(fork, cs);
+            if (eb == cudaSuccess) eb = cudaStreamWaitEvent(cs2, fork, 0);
+            for (const TbrBatchLaunch &L : b->tbr_launches)
+                if (eb == cudaSuccess) eb = batch_tbr_launch(L, b->d_grids, b->d_tbr, a.status, a.shrink, cs2);
+            if (eb == cudaSuccess) eb = cudaEventRecord(join, cs2);
+        }
         if (b->engine == JACOBI_BATCH_SWEEPS) {
-            batch_halo_kernel<<<dim3(64, (unsigned)b->n), 256, 0, cs>>>(b->d_grids, a.status, a.shrink);
             for (int p = 0; p < b->max_T; ++p)
                 batch_sweep_kernel<<<dim3(gx, gy), kSweepThreads, 0, cs>>>(
                     b->d_grids, b->d_tab, b->n64, b->n32, b->u64, b->u32, p, b->kz, a.status, a.shrink);
         } else {
-            cudaMemsetAsync(b->d_ctl, 0, sizeof(int), cs);
-            cudaMemsetAsync(b->d_ctl + 2, 0, sizeof(int) * (size_t)b->total_tiles, cs);
-            batch_halo_kernel<<<dim3(64, (unsigned)b->n), 256, 0, cs>>>(b->d_grids, a.status, a.shrink);
             batch_kernel<<<b->persistent_blocks, 256, 0, cs>>>(a);
         }
+        if (branch && eb == cudaSuccess) eb = cudaStreamWaitEvent(cs, join, 0);
         e = cudaStreamEndCapture(cs, &b->graph);
+        if (e == cudaSuccess && eb != cudaSuccess) e = eb;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    cudaEventDestroy(fork);
+    cudaEventDestroy(join);
+    cudaStreamDestroy(cs2);
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) {
         g_batch_err = cudaGetErrorString(e);
@@ -491,6 +535,7 @@ int jacobi_batch_create(jacobi_batch_h *out, int n, const int *nx, const int *ny
         cudaFree(b->d_grids);
         if (b->d_ctl) cudaFree(b->d_ctl);
         if (b->d_tab) cudaFree(b->d_tab);
+        if (b->d_tbr) cudaFree(b->d_tbr);
         delete b;
         return st;
     }
@@ -505,6 +550,7 @@ int jacobi_batch_destroy(jacobi_batch_h b)
     if (b->d_grids) cudaFree(b->d_grids);
     if (b->d_ctl) cudaFree(b->d_ctl);
     if (b->d_tab) cudaFree(b->d_tab);
+    if (b->d_tbr) cudaFree(b->d_tbr);
     delete b;
     return JACOBI_OK;
 }
@@ -515,6 +561,10 @@ int jacobi_batch_run_rhs(jacobi_batch_h b, void *const *A, void *const *B, const
     if (!b || !A || !B) return JACOBI_ERR_ARG;
     for (int g = 0; g < b->n; ++g) {
         if (!A[g] || !B[g] || A[g] == B[g]) return JACOBI_ERR_ARG;
+        // the blocked FP32 passes have no source term
+        if (RHS && RHS[g] && !engine_grid(b, b->grids[(size_t)g])) return JACOBI_ERR_UNSUPPORTED;
+    }
+    for (int g = 0; g < b->n; ++g) {
         b->grids[(size_t)g].A = A[g];
         b->grids[(size_t)g].B = B[g];
         b->grids[(size_t)g].rhs = RHS ? RHS[g] : nullptr;
@@ -553,6 +603,21 @@ int jacobi_batch_set_engine(jacobi_batch_h b, int engine, int kz)
     if (kz > 0) b->kz = kz;
     layout(b);
     return build_graph(b);
+}
+
+int jacobi_batch_set_fp32_depth(jacobi_batch_h b, int depth)
+{
+    if (!b || depth < 1 || depth > 4) return JACOBI_ERR_ARG;
+    b->fp32_depth = depth;
+    layout(b);
+    return build_graph(b);
+}
+
+int jacobi_batch_get_fp32_depth(jacobi_batch_h b, int *depth)
+{
+    if (!b || !depth) return JACOBI_ERR_ARG;
+    *depth = b->fp32_depth;
+    return JACOBI_OK;
 }
 
 int jacobi_batch_get_engine(jacobi_batch_h b, int *engine, int *kz)
@@ -611,12 +676,17 @@ int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scra
     }
     double lups = 0.0;
     for (const BatchGrid &G : b->grids) lups += (double)G.nx * G.ny * G.nz * G.T;
-    // candidates: {engine, bx, by, bz or kz}
-    const int cands[][4] = {{JACOBI_BATCH_SWEEPS, 0, 0, 8},  {JACOBI_BATCH_SWEEPS, 0, 0, 16},
-                            {JACOBI_BATCH_SWEEPS, 0, 0, 32}, {JACOBI_BATCH_PERSISTENT, 32, 4, 0},
-                            {JACOBI_BATCH_PERSISTENT, 32, 8, 0}, {JACOBI_BATCH_PERSISTENT, 32, 16, 0},
-                            {JACOBI_BATCH_PERSISTENT, 64, 4, 0}, {JACOBI_BATCH_PERSISTENT, 64, 8, 0},
-                            {JACOBI_BATCH_PERSISTENT, 128, 2, 0}, {JACOBI_BATCH_PERSISTENT, 32, 8, 64}};
+    bool any32 = false;
+    for (const BatchGrid &G : b->grids) any32 = any32 || (G.dtype == JACOBI_F32 && G.T > 0);
+    // candidates: {engine, bx, by, bz or kz, FP32 depth}; the blocked FP32
+    // depths only where the batch has FP32 grids to sweep
+    const int cands[][5] = {{JACOBI_BATCH_SWEEPS, 0, 0, 8, 1},       {JACOBI_BATCH_SWEEPS, 0, 0, 16, 1},
+                            {JACOBI_BATCH_SWEEPS, 0, 0, 32, 1},      {JACOBI_BATCH_PERSISTENT, 32, 4, 0, 1},
+                            {JACOBI_BATCH_PERSISTENT, 32, 8, 0, 1},  {JACOBI_BATCH_PERSISTENT, 32, 16, 0, 1},
+                            {JACOBI_BATCH_PERSISTENT, 64, 4, 0, 1},  {JACOBI_BATCH_PERSISTENT, 64, 8, 0, 1},
+                            {JACOBI_BATCH_PERSISTENT, 128, 2, 0, 1}, {JACOBI_BATCH_PERSISTENT, 32, 8, 64, 1},
+                            {JACOBI_BATCH_SWEEPS, 0, 0, 16, 2},      {JACOBI_BATCH_SWEEPS, 0, 0, 16, 3},
+                            {JACOBI_BATCH_SWEEPS, 0, 0, 32, 2},      {JACOBI_BATCH_SWEEPS, 0, 0, 32, 3}};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return JACOBI_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -624,8 +694,10 @@ int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scra
         return JACOBI_ERR_CUDA;
     }
     double best = -1.0;
-    int beng = b->engine, bkz = b->kz, bbx = b->bx, bby = b->by, bbz = b->bz, st = JACOBI_OK;
+    int beng = b->engine, bkz = b->kz, bbx = b->bx, bby = b->by, bbz = b->bz, bdep = b->fp32_depth, st = JACOBI_OK;
     for (const auto &t : cands) {
+        if (t[4] > 1 && !any32) continue;
+        b->fp32_depth = t[4];
         if (t[0] == JACOBI_BATCH_SWEEPS) {
             b->bx = bbx;
             b->by = bby;
@@ -652,6 +724,7 @@ int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scra
         if (g > best) {
             best = g;
             beng = t[0];
+            bdep = t[4];
             if (t[0] == JACOBI_BATCH_SWEEPS) {
                 bkz = t[3];
             } else {
@@ -666,6 +739,7 @@ int jacobi_batch_tune(jacobi_batch_h b, void *const *scratchA, void *const *scra
     if (st != JACOBI_OK) return st;
     if (glups) *glups = best;
     b->engine = beng;
+    b->fp32_depth = bdep;
     b->kz = bkz;
     b->bx = bbx;
     b->by = bby;

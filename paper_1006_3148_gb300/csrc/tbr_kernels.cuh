@@ -130,8 +130,9 @@ struct TbrMinBlocks {
     static constexpr int value = (NT == 128 && D <= 2) ? 3 : 1;
 };
 
+// The work of one CTA: tile (tix, tiy) in x and y, z chunk tiz.
 template <int D, int TX, int TY, int A>
-__global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr_pass_kernel(const TbrArgs a)
+__device__ __forceinline__ void tbr_cta(const TbrArgs &a, int tix, int tiy, int tiz)
 {
     constexpr int VY = kTbrVY, R = tbr_ring(D), NT = TX * TY;
     constexpr int W = 4 * TX, H = VY * TY;
@@ -144,9 +145,9 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
     float *bufs = tbr_smem + R * RING;         // [parity][level][LEV]
 
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-    const int xa = a.x_first + (int)blockIdx.x * a.bx;  // region origin (multiple of A)
-    const int ya = 1 - D + (int)blockIdx.y * a.by;
-    const int z0 = 1 + (int)blockIdx.z * a.bz;
+    const int xa = a.x_first + tix * a.bx;  // region origin (multiple of A)
+    const int ya = 1 - D + tiy * a.by;
+    const int z0 = 1 + tiz * a.bz;
     const int z1 = min(z0 + a.bz, a.nz + 1);
     const int xo = xa + a.off + D, yo = ya + D;         // output tile origin
     const int gx0 = xa + 4 * tx;
@@ -390,6 +391,12 @@ __global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr
         }
     }
     cp_async_wait_group<0>();
+}
+
+template <int D, int TX, int TY, int A>
+__global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr_pass_kernel(const TbrArgs a)
+{
+    tbr_cta<D, TX, TY, A>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
 }
 
 }  // namespace jac

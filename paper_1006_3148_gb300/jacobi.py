@@ -83,6 +83,8 @@ def load(build_if_missing: bool = True):
             "jacobi_batch_set_tile": ([P, i, i, i], i),
             "jacobi_batch_set_engine": ([P, i, i], i),
             "jacobi_batch_get_engine": ([P, pi, pi], i),
+            "jacobi_batch_set_fp32_depth": ([P, i], i),
+            "jacobi_batch_get_fp32_depth": ([P, pi], i),
             "jacobi_batch_run_rhs": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P], i),
             "jacobi_batch_tune": ([P, ctypes.POINTER(P), ctypes.POINTER(P), P, ctypes.POINTER(d)], i),
             "jacobi_batch_get_info": ([P, pi, pi, pi, ctypes.POINTER(ctypes.c_longlong), pi], i),
@@ -333,6 +335,17 @@ def jacobi_batch_get_engine(b: Batch) -> dict:
     e, kz = ctypes.c_int(), ctypes.c_int()
     _check(load().jacobi_batch_get_engine(b.ptr, ctypes.byref(e), ctypes.byref(kz)), "jacobi_batch_get_engine")
     return {"engine": e.value, "kz": kz.value}
+
+
+def jacobi_batch_set_fp32_depth(b: Batch, depth: int):
+    """FP32 grids in temporally blocked passes of depth <= depth (1: the engine)."""
+    _check(load().jacobi_batch_set_fp32_depth(b.ptr, int(depth)), "jacobi_batch_set_fp32_depth")
+
+
+def jacobi_batch_get_fp32_depth(b: Batch) -> int:
+    d = ctypes.c_int()
+    _check(load().jacobi_batch_get_fp32_depth(b.ptr, ctypes.byref(d)), "jacobi_batch_get_fp32_depth")
+    return d.value
 
 
 def jacobi_batch_run_rhs(b: Batch, A, B, RHS, stream=None):

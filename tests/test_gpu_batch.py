@@ -151,3 +151,59 @@ def test_batch_workload_256_grids_32_to_192():
     _check(b, hosts, Ts, expected=exp)
     J.jacobi_batch_set_tile(b, 32, 8)  # the persistent engine, same results
     _check(b, hosts, Ts, tol_fp64=False, expected=exp)
+    # FP32 grids in blocked passes beside either engine: bit-identical
+    for d in (2, 3):
+        J.jacobi_batch_set_fp32_depth(b, d)
+        _check(b, hosts, Ts, tol_fp64=False, expected=exp)
+    J.jacobi_batch_set_engine(b, J.BATCH_SWEEPS, 16)
+    _check(b, hosts, Ts, tol_fp64=False, expected=exp)
+    b.close()
+
+
+@pytest.mark.parametrize("depth", [2, 3, 4])
+def test_small_mixed_batch_fp32_depth(depth):
+    # odd and even row pitches (copy pieces of one and two cells), grids
+    # smaller than one region and than the halo margin, T from 0 to 9 so that
+    # both pass-count parities and remainder passes occur
+    rng = np.random.default_rng(11 + depth)
+    n = 19
+    dims = [tuple(int(v) for v in rng.integers(1, 90, size=3)) for _ in range(n)]
+    dims += [(1, 1, 1), (2, 1, 3), (130, 3, 2), (63, 61, 131)]
+    f32 = [bool(v) for v in rng.integers(0, 2, size=n)] + [True] * 4
+    Ts = [int(v) for v in rng.integers(0, 10, size=n)] + [3, 0, 5, 2 * depth + 1]
+    hosts = _make(dims, f32, 90)
+    b = J.Batch(dims, [torch.float32 if f else torch.float64 for f in f32], Ts)
+    J.jacobi_batch_set_fp32_depth(b, depth)
+    assert J.jacobi_batch_get_fp32_depth(b) == depth
+    for engine in (J.BATCH_SWEEPS, J.BATCH_PERSISTENT):
+        if engine == J.BATCH_PERSISTENT:
+            J.jacobi_batch_set_tile(b, 32, 8)
+        else:
+            J.jacobi_batch_set_engine(b, engine, 8)
+        _check(b, hosts, Ts)
+    b.close()
+
+
+def test_fp32_depth_all_fp32_batch_and_arguments():
+    dims = [(33, 20, 17), (64, 64, 64), (5, 70, 9)]
+    Ts = [7, 4, 1]
+    hosts = _make(dims, [True] * 3, 120)
+    b = J.Batch(dims, [torch.float32] * 3, Ts)
+    L = J.load()
+    assert L.jacobi_batch_set_fp32_depth(b.ptr, 0) == -1
+    assert L.jacobi_batch_set_fp32_depth(b.ptr, 5) == -1
+    J.jacobi_batch_set_fp32_depth(b, 3)  # no grid left for the engine
+    _check(b, hosts, Ts)
+    # no source term on the blocked FP32 passes; depth 1 takes it again
+    A = [h.cuda() for h in hosts]
+    B = [torch.empty_like(x) for x in A]
+    R = [torch.zeros_like(x) for x in A]
+    with pytest.raises(RuntimeError):
+        J.jacobi_batch_run_rhs(b, A, B, R)
+    J.jacobi_batch_run_rhs(b, A, B, [None] * 3)
+    torch.cuda.synchronize()
+    J.jacobi_batch_set_fp32_depth(b, 1)
+    J.jacobi_batch_run_rhs(b, A, B, R)
+    torch.cuda.synchronize()
+    assert J.jacobi_batch_get_status(b) == 0
+    b.close()

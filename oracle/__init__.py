@@ -15,6 +15,9 @@ Every function and the passage it follows:
   jacobi_pipelined(...)      pipelined temporal blocking order (Sect. 2.1,
                              Fig. 1; distances of Eq. 3, Sect. 2.2)
   jacobi_multihalo(...)      multi-layer halo decomposition (Sect. 3.1)
+  jacobi_compressed(A0, T)   compressed grid: one array, results shifted by
+                             (-1,-1,-1) / (+1,+1,+1) on alternate sweeps with
+                             the loops reversed (Sect. 2.1), sequential
   poisson_residual(u, f, h)  r = f - A_h u, 7-point Laplacian
   norm2(x)                   interior Euclidean norm
   poisson_jacobi(u, f, h, n) plain FP64 Jacobi for -Lap_h u = f
@@ -62,6 +65,8 @@ def lib():
             L.oracle_halo_copy_f64.argtypes = [P, P, l, l, l]
             L.oracle_jacobi_pipelined_f64.argtypes = [P, P, l, l, l, l, l, l, l, l, l, l, l, l]
             L.oracle_jacobi_multihalo_f64.argtypes = [P, P, l, l, l, P, l, l, l]
+            L.oracle_jacobi_compressed_f64.argtypes = [P, l, l, l, l]
+            L.oracle_jacobi_compressed_f32.argtypes = [P, l, l, l, l]
             L.oracle_poisson_residual.argtypes = [P, P, P, l, l, l, d]
             L.oracle_poisson_residual.restype = None
             L.oracle_norm2_interior.argtypes = [P, l, l, l]
@@ -130,6 +135,23 @@ def jacobi_multihalo(A, B, depths, bx, by) -> int:
     if r < 0:
         raise ValueError("oracle_jacobi_multihalo: bad arguments")
     return r
+
+
+def jacobi_compressed(A0, T: int):
+    """T sweeps of grid A0 (FP64 or FP32, halo included) in ONE array of
+    (nx+3)(ny+3)(nz+3) cells by the sequential compressed grid (Sect. 2.1);
+    returns the result grid (a copy taken out of that array)."""
+    a = np.asarray(A0.numpy() if hasattr(A0, "numpy") else A0)
+    dt = np.float32 if a.dtype == np.float32 else np.float64
+    a = np.ascontiguousarray(a, dtype=dt)
+    nz, ny, nx = (s - 2 for s in a.shape)
+    E = np.zeros((nz + 3, ny + 3, nx + 3), dtype=dt)
+    E[1:, 1:, 1:] = a
+    f = lib().oracle_jacobi_compressed_f32 if dt == np.float32 else lib().oracle_jacobi_compressed_f64
+    pos = f(E.ctypes.data, nx, ny, nz, int(T))
+    if pos < 0:
+        raise ValueError("bad arguments")
+    return E[pos:pos + nz + 2, pos:pos + ny + 2, pos:pos + nx + 2].copy()
 
 
 def poisson_residual(u, f, h: float) -> np.ndarray:

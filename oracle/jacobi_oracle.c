@@ -442,3 +442,97 @@ int oracle_refine(double *u, const double *f, long nx, long ny, long nz, double 
     free(r); free(g); free(e0); free(e1);
     return status;
 }
+
+/* ------------------------------------------------------- compressed grid */
+
+/* The compressed grid of Sect. 2.1, run sequentially: ONE array E of
+ * (nx+3)(ny+3)(nz+3) cells holds the grid (halo included, indices 0..n+1
+ * per axis), shifted by one cell along every axis on alternate sweeps.
+ * Position 1: cell (i,j,k) at E(i+1, j+1, k+1); position 0: at E(i, j, k).
+ * A sweep from position 1 writes every cell to position 0, i.e. shifted by
+ * (-1,-1,-1), with the loops over k, j, i running upward; a sweep from
+ * position 0 writes shifted by (+1,+1,+1) with the loops running downward.
+ * Halo cells are carried along unchanged; interior cells get Eq. (1) with
+ * the term order and division of sweep_f64 / sweep_f32.  A write destroys
+ * the old value of the cell one step back along every axis (in loop
+ * direction), and every cell that reads that value (its six neighbours and,
+ * for a halo cell, itself) comes earlier in the loop order.  Returns the
+ * position of the result: 1 if T is even, else 0. */
+#define EIDX(i, j, k) ((((k) * (ny + 3)) + (j)) * (nx + 3) + (i))
+
+static void cg_sweep_f64(double *E, long nx, long ny, long nz, long from)
+{
+    const long o = from, w = 1 - from;
+    for (long kk = 0; kk <= nz + 1; ++kk) {
+        const long k = from ? kk : nz + 1 - kk;
+        for (long jj = 0; jj <= ny + 1; ++jj) {
+            const long j = from ? jj : ny + 1 - jj;
+            for (long ii = 0; ii <= nx + 1; ++ii) {
+                const long i = from ? ii : nx + 1 - ii;
+                double v;
+                if (is_halo(i, j, k, nx, ny, nz)) {
+                    v = E[EIDX(i + o, j + o, k + o)];
+                } else {
+                    double s = E[EIDX(i - 1 + o, j + o, k + o)];
+                    s = s + E[EIDX(i + 1 + o, j + o, k + o)];
+                    s = s + E[EIDX(i + o, j - 1 + o, k + o)];
+                    s = s + E[EIDX(i + o, j + 1 + o, k + o)];
+                    s = s + E[EIDX(i + o, j + o, k - 1 + o)];
+                    s = s + E[EIDX(i + o, j + o, k + 1 + o)];
+                    v = s / 6.0;
+                }
+                E[EIDX(i + w, j + w, k + w)] = v;
+            }
+        }
+    }
+}
+
+static void cg_sweep_f32(float *E, long nx, long ny, long nz, long from)
+{
+    const float sixth = 1.0f / 6.0f; /* RN_f32(1/6) */
+    const long o = from, w = 1 - from;
+    for (long kk = 0; kk <= nz + 1; ++kk) {
+        const long k = from ? kk : nz + 1 - kk;
+        for (long jj = 0; jj <= ny + 1; ++jj) {
+            const long j = from ? jj : ny + 1 - jj;
+            for (long ii = 0; ii <= nx + 1; ++ii) {
+                const long i = from ? ii : nx + 1 - ii;
+                float v;
+                if (is_halo(i, j, k, nx, ny, nz)) {
+                    v = E[EIDX(i + o, j + o, k + o)];
+                } else {
+                    float s = E[EIDX(i - 1 + o, j + o, k + o)];
+                    s = s + E[EIDX(i + 1 + o, j + o, k + o)];
+                    s = s + E[EIDX(i + o, j - 1 + o, k + o)];
+                    s = s + E[EIDX(i + o, j + 1 + o, k + o)];
+                    s = s + E[EIDX(i + o, j + o, k - 1 + o)];
+                    s = s + E[EIDX(i + o, j + o, k + 1 + o)];
+                    v = s * sixth;
+                }
+                E[EIDX(i + w, j + w, k + w)] = v;
+            }
+        }
+    }
+}
+
+int oracle_jacobi_compressed_f64(double *E, long nx, long ny, long nz, long T)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || T < 0) return -1;
+    long pos = 1;
+    for (long s = 0; s < T; ++s) {
+        cg_sweep_f64(E, nx, ny, nz, pos);
+        pos = 1 - pos;
+    }
+    return (int)pos;
+}
+
+int oracle_jacobi_compressed_f32(float *E, long nx, long ny, long nz, long T)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || T < 0) return -1;
+    long pos = 1;
+    for (long s = 0; s < T; ++s) {
+        cg_sweep_f32(E, nx, ny, nz, pos);
+        pos = 1 - pos;
+    }
+    return (int)pos;
+}

@@ -304,6 +304,42 @@ int jacobi_refine(jacobi_h h, double *u, const double *f, double hgrid, double r
 int jacobi_poisson_residual_noalloc(const void *u, const void *f, int nx, int ny, int nz,
                                     double hgrid, jacobi_stream_t stream, double *rel);
 
+/* ------------------------------------------------------- compressed grid
+ * Sweeps in ONE buffer, without the second grid (the compressed grid of
+ * Sect. 2.1).  The buffer U holds nz + 2 + S planes of (nx+2)(ny+2)
+ * elements of the handle's dtype; the grid (the usual layout, halo
+ * included) sits either in the UPPER position (its plane k at buffer plane
+ * k + S, i.e. starting S*(nx+2)*(ny+2) elements into U) or in the LOWER
+ * position (starting at U).  Each pass of `depth` sweeps reads the grid in
+ * one position and leaves the result, halo included, in the other: the
+ * write shift of S planes alternates in direction, as the paper's shift by
+ * (-1,-1,-1) and (+1,+1,+1) does, and the order of the z chunks is reversed
+ * on alternate passes.  S = waves*bz + depth + 1 (jacobi_compressed_get_plan):
+ * up to `waves` chunks of bz planes are swept at once, and a chunk starts
+ * only after the chunks whose input it overwrites have finished (bounded
+ * waits: JACOBI_ERR_TIMEOUT in the status word if one runs out).  Results
+ * are bit-identical to jacobi_sweep with T sweeps. */
+
+/* Plan of the compressed sweeps: depth 1..4 sweeps per pass (FP32: the
+ * register-blocked one-CTA body of JACOBI_KERNEL_TB_REG, 64 x 32 regions;
+ * FP64: depth 1 only, else JACOBI_ERR_UNSUPPORTED), z chunk bz >= 2*depth+2,
+ * waves 1..8 (JACOBI_ERR_ARG otherwise).  Default: FP32 depth 3, FP64 depth
+ * 1; bz 64; waves 2. */
+int jacobi_compressed_set_plan(jacobi_h h, int depth, int bz, int waves);
+
+/* The current compressed plan and its shift S in planes (any may be NULL). */
+int jacobi_compressed_get_plan(jacobi_h h, int *depth, int *bz, int *waves, long long *shift_planes);
+
+/* T sweeps of the grid held in U (device pointer, 16-byte aligned, at least
+ * (nx+2)(ny+2)(nz+2+S) elements) starting in position `upper` (1: upper,
+ * 0: lower).  Runs ceil(T/depth) passes (the last one shallower if depth
+ * does not divide T); *upper_out (may be NULL) receives the position of the
+ * result: upper XOR (number of passes odd).  Cells of U outside the grid's
+ * position are scratch.  Asynchronous on stream; allocates its small
+ * counter array on first use (kept on the handle).  Calls on one handle
+ * must not overlap. */
+int jacobi_sweep_compressed(jacobi_h h, void *U, int T, int upper, int *upper_out, jacobi_stream_t stream);
+
 /* ---------------------------------------------------------------- batch
  * Many independent grids (each its own size, element type and sweep count
  * T_g), swept by a CUDA graph that one of two engines builds:

@@ -384,6 +384,7 @@ int jacobi_destroy(jacobi_h h)
     if (h->hostA) cudaFree(h->hostA);
     if (h->hostB) cudaFree(h->hostB);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->cg_ctl) cudaFree(h->cg_ctl);
     free_poisson_scratch(h);
     delete h;
     return JACOBI_OK;
@@ -497,6 +498,42 @@ int jacobi_debug_set_fault(jacobi_h h, int mode, int limit_ms)
 }
 
 int jacobi_build_checked(void) { return kChecked ? 1 : 0; }
+
+namespace {
+int cg_depth_of(const jacobi_plan_s *h) { return h->cg_depth > 0 ? h->cg_depth : (h->dtype == JACOBI_F64 ? 1 : 3); }
+}  // namespace
+
+int jacobi_compressed_set_plan(jacobi_h h, int depth, int bz, int waves)
+{
+    if (!h) return JACOBI_ERR_ARG;
+    const int st = cg_check(h, depth, bz, waves);
+    if (st != JACOBI_OK) return st;
+    h->cg_depth = depth;
+    h->cg_bz = bz;
+    h->cg_waves = waves;
+    return JACOBI_OK;
+}
+
+int jacobi_compressed_get_plan(jacobi_h h, int *depth, int *bz, int *waves, long long *shift_planes)
+{
+    if (!h) return JACOBI_ERR_ARG;
+    const int d = cg_depth_of(h);
+    if (depth) *depth = d;
+    if (bz) *bz = h->cg_bz;
+    if (waves) *waves = h->cg_waves;
+    if (shift_planes) *shift_planes = cg_shift_planes(d, h->cg_bz, h->cg_waves);
+    return JACOBI_OK;
+}
+
+int jacobi_sweep_compressed(jacobi_h h, void *U, int T, int upper, int *upper_out, jacobi_stream_t stream)
+{
+    if (!h || !U || T < 0 || (upper != 0 && upper != 1)) return JACOBI_ERR_ARG;
+    if (!aligned16(U)) return JACOBI_ERR_ALIGN;
+    h->cg_depth = cg_depth_of(h);
+    const int st = cg_check(h, h->cg_depth, h->cg_bz, h->cg_waves);
+    if (st != JACOBI_OK) return st;
+    return cg_sweep(h, U, T, upper, upper_out, (cudaStream_t)stream);
+}
 
 int jacobi_profile_enable(jacobi_h h, int enable)
 {

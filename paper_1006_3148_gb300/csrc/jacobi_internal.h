@@ -157,6 +157,11 @@ struct jacobi_plan_s {
     size_t ev_used = 0;
     int prof_pass = 0, prof_other = 0;
     long long check_shrink = 0;  // checked build test hook (jacobi_debug_set_fault mode 2)
+    // compressed grid: depth (0: 3 for FP32, 1 for FP64), z chunk, chunk
+    // waves; item ticket and per-chunk completion counters
+    int cg_depth = 0, cg_bz = 64, cg_waves = 2;
+    int *cg_ctl = nullptr;
+    size_t cg_ctl_n = 0;
     // Poisson / refinement scratch (allocated on first use, freed by destroy)
     void *g = nullptr;          // source term h^2 r (FP32) or h^2 f (FP64)
     void *e0 = nullptr, *e1 = nullptr;  // FP32 correction grids
@@ -169,5 +174,9 @@ struct jacobi_plan_s {
 
 namespace jac {
 void free_poisson_scratch(jacobi_plan_s *h);
+// compressed grid (compressed.cu)
+long long cg_shift_planes(int depth, int bz, int waves);
+int cg_check(const jacobi_plan_s *h, int depth, int bz, int waves);
+int cg_sweep(jacobi_plan_s *h, void *U, int T, int upper, int *upper_out, cudaStream_t s);
 }
 

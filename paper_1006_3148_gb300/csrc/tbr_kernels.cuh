@@ -211,8 +211,11 @@ __device__ __forceinline__ void tbr_cta(const TbrArgs &a, int tix, int tiy, int 
     const int cp_off0 = (ya + cp_row) * P + cp_gx;  // plane offset of copy 0 (used only if inside)
     const uint32_t cp_dst0 = smem_addr(ring + cp_row * W + cp_col);
     // FAST: the whole region lies inside the array, so every piece is copied.
+    // planes beyond z1 - 1 + D feed only the steps past the chunk: not
+    // loaded (their ring slots keep older planes, never stored)
+    const int p_hi = min(a.nz + 1, z1 - 1 + D);
     auto load_plane = [&](int p, auto FAST) {
-        if (p >= 0 && p <= a.nz + 1) {
+        if (p >= 0 && p <= p_hi) {
             const float *sp = src + (long long)p * plane;
             const uint32_t d0 = cp_dst0 + (uint32_t)((p & (R - 1)) * RING * 4);
 #pragma unroll
@@ -374,8 +377,8 @@ __device__ __forceinline__ void tbr_cta(const TbrArgs &a, int tix, int tiy, int 
         }
     };
     // Whole rotations of three steps; the up to two extra steps at the end
-    // compute planes beyond the chunk (never stored; their loads beyond the
-    // array are skipped), so no step needs a guard.
+    // compute planes beyond the chunk (never stored; their loads are
+    // skipped), so no step needs a guard.
     if (interior) {
         const std::true_type f;
         for (int t = 0; t < nsteps; t += 3) {

@@ -83,6 +83,9 @@ def load(build_if_missing: bool = True):
             "jacobi_batch_set_tile": ([P, i, i, i], i),
             "jacobi_batch_set_engine": ([P, i, i], i),
             "jacobi_batch_get_engine": ([P, pi, pi], i),
+            "jacobi_compressed_set_plan": ([P, i, i, i], i),
+            "jacobi_compressed_get_plan": ([P, pi, pi, pi, ctypes.POINTER(ctypes.c_longlong)], i),
+            "jacobi_sweep_compressed": ([P, P, i, i, pi, P], i),
             "jacobi_batch_set_fp32_depth": ([P, i], i),
             "jacobi_batch_get_fp32_depth": ([P, pi], i),
             "jacobi_batch_run_rhs": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P], i),
@@ -335,6 +338,43 @@ def jacobi_batch_get_engine(b: Batch) -> dict:
     e, kz = ctypes.c_int(), ctypes.c_int()
     _check(load().jacobi_batch_get_engine(b.ptr, ctypes.byref(e), ctypes.byref(kz)), "jacobi_batch_get_engine")
     return {"engine": e.value, "kz": kz.value}
+
+
+def jacobi_compressed_set_plan(h: Handle, depth: int, bz: int = 64, waves: int = 2):
+    _check(load().jacobi_compressed_set_plan(h.ptr, int(depth), int(bz), int(waves)), "jacobi_compressed_set_plan")
+
+
+def jacobi_compressed_get_plan(h: Handle) -> dict:
+    d, bz, w, S = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _check(load().jacobi_compressed_get_plan(h.ptr, ctypes.byref(d), ctypes.byref(bz), ctypes.byref(w),
+                                             ctypes.byref(S)), "jacobi_compressed_get_plan")
+    return {"depth": d.value, "bz": bz.value, "waves": w.value, "shift_planes": S.value}
+
+
+def compressed_buffer(h: Handle, device="cuda") -> torch.Tensor:
+    """An uninitialised buffer for jacobi_sweep_compressed: nz + 2 + S planes."""
+    S = jacobi_compressed_get_plan(h)["shift_planes"]
+    return torch.empty((h.nz + 2 + S, h.ny + 2, h.nx + 2), dtype=h.dtype, device=device)
+
+
+def compressed_view(h: Handle, U: torch.Tensor, upper: int) -> torch.Tensor:
+    """The grid inside U in position `upper` (1: planes S .. S+nz+1, 0: 0 .. nz+1)."""
+    S = jacobi_compressed_get_plan(h)["shift_planes"]
+    o = S if upper else 0
+    return U[o:o + h.nz + 2]
+
+
+def jacobi_sweep_compressed(h: Handle, U: torch.Tensor, T: int, upper: int = 1, stream=None) -> int:
+    """T sweeps in the single buffer U (see compressed_buffer); returns the
+    position of the result (1: upper, 0: lower)."""
+    S = jacobi_compressed_get_plan(h)["shift_planes"]
+    need = (h.nz + 2 + S) * (h.ny + 2) * (h.nx + 2)
+    if not U.is_cuda or not U.is_contiguous() or U.numel() < need or U.dtype != h.dtype:
+        raise ValueError("U: contiguous CUDA tensor of %d elements of the handle's dtype" % need)
+    out = ctypes.c_int()
+    _check(load().jacobi_sweep_compressed(h.ptr, ctypes.c_void_p(U.data_ptr()), int(T), int(upper),
+                                          ctypes.byref(out), _stream(stream)), "jacobi_sweep_compressed")
+    return out.value
 
 
 def jacobi_batch_set_fp32_depth(b: Batch, depth: int):

@@ -72,6 +72,8 @@ WORKLOADS = {
                     name="jacobi3d_fp64_64cubed_T10"),
     "fp32_1024": dict(n=(1024, 1024, 1024), dtype="f32", T=200, gen="mode", seed=3,
                       name="jacobi3d_fp32_1024cubed_T200_mode16"),
+    "compressed1024": dict(n=(1024, 1024, 1024), dtype="f32", T=200, gen="mode", seed=3,
+                           name="jacobi3d_fp32_1024cubed_T200_mode16_compressed_grid"),
     "batch256": dict(n=None, dtype="mixed", T=50, gen="batch", seed=4,
                      name="jacobi3d_batch_256grids_32to192_half_fp64_T50"),
     "poisson96": dict(n=(96, 96, 96), dtype="f64", T=500, gen="poisson", seed=5,
@@ -667,6 +669,70 @@ def run_batch(args, w, ctx, sub=False):
     return line
 
 
+def run_compressed(args, w, ctx, sub=False):
+    """The FP32 1024^3 workload swept in ONE buffer (compressed grid,
+    jacobi_sweep_compressed): one step = T sweeps, the grid moving between
+    its two positions in the buffer pass by pass."""
+    import torch
+    from paper_1006_3148_gb300 import jacobi as J
+
+    dist, ws, dev = ctx.dist, ctx.ws, ctx.dev
+    nx, ny, nz = w["n"]
+    T = w["T"]
+    es = 8 if w["dtype"] == "f64" else 4
+    dt = torch.float64 if w["dtype"] == "f64" else torch.float32
+    h = J.Handle(nx, ny, nz, dt)
+    if args.cg_plan:
+        J.jacobi_compressed_set_plan(h, *(int(v) for v in args.cg_plan.split(":")))
+    cg = J.jacobi_compressed_get_plan(h)
+    U = J.compressed_buffer(h, device=dev)
+    J.compressed_view(h, U, 1).copy_(_make_grid(w, dev))
+    stream = torch.cuda.current_stream()
+    pos = 1
+    for _ in range(args.warmup):
+        pos = J.jacobi_sweep_compressed(h, U, T, pos, stream)
+    ctx.barrier()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    ctx.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        pos = J.jacobi_sweep_compressed(h, U, T, pos, stream)
+    e1.record(stream)
+    ctx.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    assert J.jacobi_get_status(h) == 0, "device status word set during the timed region"
+    ms = reduce_max(dist, ms, dev)
+    value = aggregate_glups(ws, nx * ny * nz * T, args.steps, ms)
+    passes = (T + cg["depth"] - 1) // cg["depth"]
+    # one pass kernel per pass (plus a counter reset); its algorithmic bytes:
+    # the grid read and written once
+    pass_ms = ms / args.steps / passes
+    peaks, peak_src = _peaks()
+    m_s = float(peaks.get("hbm_gbs", M_S_FALLBACK))
+    hbm_ach = 2.0 * es * nx * ny * nz / (pass_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": hbm_ach, "peak": m_s, "unit": "GB/s", "frac": hbm_ach / m_s,
+            "traffic": None, "peak_source": peak_src, "kernel": "cg_f32_kernel" if es == 4 else "cg_f64_kernel",
+            "avg_launch_ms": pass_ms,
+            "note": "algorithmic bytes: read and write the grid once per pass (2 x %d B per cell); pass time = "
+                    "step time / passes (one launch per pass and a counter reset)" % es}
+    grid_bytes = (nx + 2) * (ny + 2) * (nz + 2) * es
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic", "config": grid_config(w, ws),
+        "plan": dict(cg, memory_vs_one_grid=U.numel() * es / grid_bytes, memory_vs_two_grids=U.numel() * es / (2 * grid_bytes)),
+        "roofline": roof, "gpu_launches": passes * args.steps, "clocks": clocks,
+    }
+    h.close()
+    del U
+    torch.cuda.empty_cache()
+    return line
+
+
 def run_poisson(args, w, ctx):
     """-Lap u = f, 96^3, h = 1/97, f ~ N(0,1), zero halo: time to a relative
     residual of 1e-10 by mixed-precision refinement (FP64 residual/update,
@@ -742,6 +808,7 @@ def main():
     ap.add_argument("--workload", default="fp64_512", choices=sorted(WORKLOADS))
     ap.add_argument("--plan", default=None, help="force a plan kernel:depth:bx:by:bz[:ring[:threads]], kernel tb, cta, "
                     "reg, chain (ring = CTAs), plain or x2, e.g. tb:4:64:16:64:8, cta:4:64:32:64:0:512 or x2:1:32:8:16")
+    ap.add_argument("--cg-plan", default=None, help="compressed grid plan depth:bz:waves")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -773,12 +840,16 @@ def main():
             line = run_batch(args, w, ctx)
         elif w["gen"] == "poisson":
             line = run_poisson(args, w, ctx)
+        elif args.workload == "compressed1024":
+            line = run_compressed(args, w, ctx)
         else:
             line = run_ours(args, w, ctx)
             if args.workload == "fp64_512" and not resized and not args.no_sub and not args.plan:
                 # the FP32 and batched workloads, measured in the same run
                 line["fp32_1024"] = sub_line(run_ours(args, dict(WORKLOADS["fp32_1024"]), ctx, sub=True))
                 line["batch256"] = sub_line(run_batch(args, dict(WORKLOADS["batch256"]), ctx, sub=True))
+                line["compressed_fp32_1024"] = sub_line(
+                    run_compressed(args, dict(WORKLOADS["compressed1024"]), ctx, sub=True))
         if ctx.rank == 0:
             print(json.dumps(line), flush=True)
     finally:

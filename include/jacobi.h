@@ -241,7 +241,7 @@ int jacobi_debug_set_fault(jacobi_h h, int mode, int limit_ms);
 
 /* 1 if this library is the bounds-checked build (compiled with
  * -DJACOBI_CHECKED: every global, shared and distributed shared memory
- * access of the sweep, batch and refinement kernels is checked against its
+ * access of the sweep, batch, compressed-grid and refinement kernels is checked against its
  * buffer, and an access outside records JACOBI_ERR_BOUNDS in the status word
  * and is skipped instead of performed), else 0. */
 int jacobi_build_checked(void);

@@ -1,7 +1,7 @@
 """The bounds-checked build (compiled with -DJACOBI_CHECKED).
 
 Every global, shared and distributed-shared-memory access of the sweep,
-batch and refinement kernels is checked against the buffer it belongs to;
+batch, compressed-grid and refinement kernels is checked against the buffer it belongs to;
 an access outside records JACOBI_ERR_BOUNDS in the status word and is
 skipped (no trap).  This stands in for a memory checker.  The checked library is built
 beside the normal one (libjacobi_checked.so) and the small-shape parity
@@ -53,7 +53,7 @@ def test_checked_build_parity_suites_status_zero(checked_build):
     # timing tests left out: the checked kernels are slow)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "gpu",
                         "tests/test_gpu_sweep.py", "tests/test_gpu_batch.py", "tests/test_gpu_refine.py",
-                        "tests/test_gpu_plans.py",
+                        "tests/test_gpu_plans.py", "tests/test_gpu_compressed.py",
                         "-k", "not untuned and not 256cubed and not workload_96cubed and not 65535 and not tuner"],
                        env=CHECKED_ENV, cwd=ROOT, capture_output=True, text=True, timeout=3600)
     assert r.returncode == 0, r.stdout[-4000:]
@@ -92,6 +92,22 @@ A = [inputs.uniform_grid(*d, seed=9).to(t).cuda() for d, t in zip(dims, (torch.f
 J.jacobi_batch_run(b, A, [torch.empty_like(x) for x in A])
 torch.cuda.synchronize()
 assert J.jacobi_batch_get_status(b) == -6
+for dt, plan in ((torch.float32, (2, 6, 2)), (torch.float64, (1, 4, 2))):
+    h = J.Handle(*shape, dt)
+    J.jacobi_compressed_set_plan(h, *plan)
+    U = J.compressed_buffer(h)
+    a0 = inputs.uniform_grid(*shape, seed=6, dtype=torch.float64).to(dt)
+    J.compressed_view(h, U, 1).copy_(a0)
+    J.jacobi_debug_set_fault(h, 2, 2000)
+    J.jacobi_sweep_compressed(h, U, 3, 1)
+    torch.cuda.synchronize()
+    assert J.jacobi_get_status(h) == -6, dt
+    J.jacobi_debug_set_fault(h, 0, 2000)
+    J.compressed_view(h, U, 1).copy_(a0)
+    pos = J.jacobi_sweep_compressed(h, U, 3, 1)
+    torch.cuda.synchronize()
+    assert J.jacobi_get_status(h) == 0
+    assert np.array_equal(J.compressed_view(h, U, pos).cpu().numpy(), oracle.jacobi_result(a0.numpy(), 3)), dt
 print("bounds reported")
 ''')
     assert "bounds reported" in out

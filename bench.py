@@ -61,7 +61,7 @@ MEASURED_TRAFFIC = {
     ("plain_pass_kernel", "f64", 1): (15.92, "ncu: plain_pass_kernel<double>, 512^3"),
     ("tbc4_pass_kernel", "f32", 2): (3.97, "ncu: tbc4_pass_kernel depth 2, FP32 512^3"),
     ("tbc4_pass_kernel", "f32", 4): (2.04, "ncu: tbc4_pass_kernel depth 4, FP32 512^3"),
-    ("tbr_pass_kernel", "f32", 3): (2.79, "ncu: tbr_pass_kernel depth 3, region 64x32, FP32 512^3, one pass"),
+    ("tbr_pass_kernel", "f32", 3): (2.82, "ncu: tbr_pass_kernel depth 3, region 64x32, FP32 512^3, one pass"),
 }
 SM_MAX_MHZ = 2070.0
 

@@ -16,15 +16,17 @@
 // (plus the boundary plane 0 or nz+1 for the first and last chunks), i.e.
 // input planes [z0_j - S, z0_j - S + bz + 1) in an upper-to-lower pass.  With
 // S = w*bz + D + 1 and bz >= 2D + 2 those are read only by the items of
-// chunks j-w and j-w-1.  Items are handed out in chunk order (increasing z
-// for an upper-to-lower pass, decreasing for the reverse, the counterpart
-// of the paper's reversed loops) from an atomic ticket that each CTA takes
-// when it starts, and an item starts only after every item of chunks j-w
-// and j-w-1 (j+w, j+w+1 in reverse) has finished: up to w chunks of items
-// run at once and no item overwrites a value another has yet to read.
-// Every wait is on items with smaller tickets, taken by CTAs that started
-// earlier and never wait on later ones, so the schedule cannot deadlock;
-// each wait is also bounded in time.
+// chunks j-w and j-w-1, and among them (the x-y regions reach D cells, less
+// than a tile, past their tile) only by the items of tile t and its eight
+// neighbours.  Items are handed out in chunk order (increasing z for an
+// upper-to-lower pass, decreasing for the reverse, the counterpart of the
+// paper's reversed loops) from an atomic ticket that each CTA takes when it
+// starts, and item (t, j) starts only after those up to 18 items (chunks
+// j+w, j+w+1 in reverse) have finished: no item overwrites a value another
+// has yet to read, and a column of tiles runs up to w chunks ahead of its
+// neighbours.  Every wait is on items with smaller tickets, taken by CTAs
+// that started earlier and never wait on later ones, so the schedule cannot
+// deadlock; each wait is also bounded in time.
 //
 // FP32 items run the register-blocked temporally blocked body of the
 // one-CTA kernel (tbr_kernels.cuh; 64 x 32 regions, depth 1..4); FP64 items
@@ -56,7 +58,7 @@ struct CgArgs {
     int fby;            // ... and rows 1 + tiy*fby ...
     int up;             // 1: read the upper position, write the lower one
     long long items;
-    int *head, *done, *status;
+    int *head, *done, *status;  // done[j * ntx * nty + t]: item (t, j) finished
     unsigned long long limit_ns;
     int fault_mode;
     long long shrink;
@@ -70,7 +72,7 @@ __device__ __forceinline__ int ld_acquire_gpu(const int *p)
 }
 
 // Waits until *p >= want (bounded; gives up early once the status word is
-// set).  Returns false on timeout or abort.
+// set).  Returns false on timeout or abort.  Called by several lanes at once.
 __device__ bool wait_count(const int *p, int want, unsigned long long limit_ns, const volatile int *status)
 {
     if (ld_acquire_gpu(p) >= want) return true;
@@ -86,44 +88,59 @@ __device__ bool wait_count(const int *p, int want, unsigned long long limit_ns, 
 }
 
 // Takes this CTA's item (the next ticket); returns false when none is left.
-// On return the whole CTA knows the item's column c, chunk j and whether its
-// waits held.
+// Warp 0 takes the ticket and does the waits; one barrier then hands the
+// item, its column c, chunk j and whether the waits held to the whole CTA.
 __device__ bool take_item(const CgArgs &a, long long &q, int &c, int &j, bool &ok)
 {
     __shared__ long long s_item;
     __shared__ int s_ok;
-    if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.head, 1);
+    const int ncols = a.ntx * a.nty;
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        long long item = 0;
+        if (l == 0) item = (long long)atomicAdd(a.head, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        bool good = true;
+        if (item < a.items) {
+            // lane l < 18 waits for item (tile (tix + l%3 - 1, tiy + (l/3)%3 - 1),
+            // chunk j -+ (w + l/9)), if it exists
+            const long long qq = item / ncols;
+            const int cc = (int)(item % ncols);
+            const int jc = a.up ? (int)qq : a.nch - 1 - (int)qq;
+            const int tix = cc % a.ntx, tiy = cc / a.ntx;
+            const int nx_ = tix + l % 3 - 1, ny_ = tiy + (l / 3) % 3 - 1;
+            const int jj = a.up ? jc - a.w - l / 9 : jc + a.w + l / 9;
+            if (l < 18 && nx_ >= 0 && nx_ < a.ntx && ny_ >= 0 && ny_ < a.nty && jj >= 0 && jj < a.nch)
+                good = wait_count(a.done + (long long)jj * ncols + ny_ * a.ntx + nx_, 1, a.limit_ns, a.status);
+        }
+        good = __all_sync(0xffffffffu, good);
+        if (l == 0) {
+            if (!good) atomicCAS(a.status, 0, JACOBI_ERR_TIMEOUT);
+            s_item = item;
+            s_ok = good;
+        }
+    }
     __syncthreads();
     const long long item = s_item;
-    __syncthreads();
+    ok = s_ok != 0;
     if (item >= a.items) return false;
-    const int ncols = a.ntx * a.nty;
     q = item / ncols;
     c = (int)(item % ncols);
     j = a.up ? (int)q : a.nch - 1 - (int)q;
-    if (threadIdx.x == 0) {
-        bool good = true;
-        for (int e = 0; e < 2; ++e) {
-            const int jj = a.up ? j - a.w - e : j + a.w + e;
-            if (jj >= 0 && jj < a.nch) good = good && wait_count(a.done + jj, ncols, a.limit_ns, a.status);
-        }
-        if (!good) atomicCAS(a.status, 0, JACOBI_ERR_TIMEOUT);
-        s_ok = good;
-    }
-    __syncthreads();
-    ok = s_ok != 0;
     return true;
 }
 
 // Publishes the end of an item: every thread's reads and writes of the item
-// come before the count (barrier, then a device-scope fence by one thread).
+// come before the flag (barrier, then a release store at device scope by
+// one thread, cumulative over the writes the barrier ordered before it).
 __device__ void finish_item(const CgArgs &a, long long q, int c, int j)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        // test hook: the first item never reports, so waits on its chunk run out
-        if (!(a.fault_mode == 1 && q == 0 && c == 0)) atomicAdd(a.done + j, 1);
+        // test hook: the first item never reports, so waits on it run out
+        if (!(a.fault_mode == 1 && q == 0 && c == 0))
+            asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(a.done + (long long)j * a.ntx * a.nty + c), "r"(1)
+                         : "memory");
     }
 }
 
@@ -188,40 +205,44 @@ __global__ void __launch_bounds__(128, (TbrMinBlocks<D, 128>::value)) cg_f32_ker
 
 // FP64 item: one sweep of a 32 x 8 column tile over the chunk's planes, the
 // values at k-1, k, k+1 of the thread's column in registers, the in-plane
-// neighbours read through L2.
+// neighbours by ordinary (L1-cached, coherent) loads: within a pass an
+// address is only read before it is overwritten, so no line is read stale.
 __global__ void __launch_bounds__(kCgF64X *kCgF64Y) cg_f64_kernel(const CgArgs a)
 {
     long long q;
     int c, j;
     bool ok;
     if (!take_item(a, q, c, j, ok)) return;
-    {
-        const int tix = c % a.ntx, tiy = c / a.ntx;
-        const int z0 = 1 + j * a.bz, z1 = min(z0 + a.bz, a.nz + 1);
-        if (ok) {
-            const int x = 1 + tix * kCgF64X + (int)threadIdx.x % kCgF64X;
-            const int y = 1 + tiy * kCgF64Y + (int)threadIdx.x / kCgF64X;
-            if (x <= a.nx && y <= a.ny) {
-                const double *src = static_cast<const double *>(a.src);
-                double *dst = static_cast<double *>(a.dst);
-                const long long P = a.nx + 2, plane = P * (a.ny + 2);
-                const long long SG = checked_grid_elems(a.nx, a.ny, a.nz, a.shrink);
-                auto ld = [&](long long off) { return in_bounds(off, 1, SG, a.status) ? __ldcg(src + off) : 0.0; };
-                const long long col = (long long)y * P + x;
-                double lo = ld(col + (long long)(z0 - 1) * plane), mid = ld(col + (long long)z0 * plane);
-                for (int k = z0; k < z1; ++k) {
-                    const long long o = col + (long long)k * plane;
-                    const double hi = ld(o + plane);
-                    const double v = Arith<double>::update(ld(o - 1), ld(o + 1), ld(o - P), ld(o + P), lo, hi);
-                    if (in_bounds(o, 1, SG, a.status)) dst[o] = v;
-                    lo = mid;
-                    mid = hi;
-                }
+    const int tix = c % a.ntx, tiy = c / a.ntx;
+    const int z0 = 1 + j * a.bz, z1 = min(z0 + a.bz, a.nz + 1);
+    if (ok) {
+        const int x = 1 + tix * kCgF64X + (int)threadIdx.x % kCgF64X;
+        const int y = 1 + tiy * kCgF64Y + (int)threadIdx.x / kCgF64X;
+        if (x <= a.nx && y <= a.ny) {
+            const long long P = a.nx + 2, plane = P * (a.ny + 2);
+            const long long c0 = (long long)z0 * plane + (long long)y * P + x;
+            const double *sb = static_cast<const double *>(a.src);
+            double *db = static_cast<double *>(a.dst);
+            const double *p = sb + c0;
+            double *o = db + c0;
+            const int nxp = a.nx + 2;
+            const long long SG = checked_grid_elems(a.nx, a.ny, a.nz, a.shrink);
+            auto ld = [&](const double *ptr) { return in_bounds(ptr - sb, 1, SG, a.status) ? *ptr : 0.0; };
+            double lo = ld(p - plane), mid = ld(p);
+#pragma unroll 4
+            for (int k = z0; k < z1; ++k) {
+                const double hi = ld(p + plane);
+                const double v = Arith<double>::update(ld(p - 1), ld(p + 1), ld(p - nxp), ld(p + nxp), lo, hi);
+                if (in_bounds(o - db, 1, SG, a.status)) *o = v;
+                lo = mid;
+                mid = hi;
+                p += plane;
+                o += plane;
             }
-            move_boundary<double>(a, tix, tiy, z0, z1, j == 0, j == a.nch - 1);
         }
-        finish_item(a, q, c, j);
+        move_boundary<double>(a, tix, tiy, z0, z1, j == 0, j == a.nch - 1);
     }
+    finish_item(a, q, c, j);
 }
 
 template <int D, int A>
@@ -308,7 +329,7 @@ int cg_sweep(jacobi_plan_s *h, void *U, int T, int upper, int *upper_out, cudaSt
     }
     a.items = (long long)a.ntx * a.nty * nch;
     if (a.items >= (1ll << 31) || (long long)a.ntx * a.nty >= (1ll << 31)) return JACOBI_ERR_UNSUPPORTED;
-    const size_t need = 1 + (size_t)nch;
+    const size_t need = 1 + (size_t)nch * a.ntx * a.nty;
     if (h->cg_ctl_n < need) {
         if (h->cg_ctl) cudaFree(h->cg_ctl);
         h->cg_ctl = nullptr;

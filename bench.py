@@ -253,8 +253,10 @@ def grid_config(w, ws: int) -> dict:
     """The workload's config keys, identical in both arms."""
     nx, ny, nz = w["n"]
     es = 8 if w["dtype"] == "f64" else 4
+    gb = (nx + 2) * (ny + 2) * (nz + 2) * es / 1e9
+    held = "one %.2f GB grid in one buffer" % gb if "compressed_grid" in w["name"] else "two %.2f GB grids" % gb
     return {"workload": w["name"], "nx": nx, "ny": ny, "nz": nz, "T": w["T"], "parallelism": _parallelism(ws),
-            "l2": "inputs larger than L2 (two %.2f GB grids)" % ((nx + 2) * (ny + 2) * (nz + 2) * es / 1e9)}
+            "l2": "inputs larger than L2 (%s)" % held}
 
 
 def batch_config(w, ws: int) -> dict:

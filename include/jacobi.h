@@ -315,16 +315,19 @@ int jacobi_poisson_residual_noalloc(const void *u, const void *f, int nx, int ny
  * write shift of S planes alternates in direction, as the paper's shift by
  * (-1,-1,-1) and (+1,+1,+1) does, and the order of the z chunks is reversed
  * on alternate passes.  S = waves*bz + depth + 1 (jacobi_compressed_get_plan):
- * up to `waves` chunks of bz planes are swept at once, and a chunk starts
- * only after the chunks whose input it overwrites have finished (bounded
- * waits: JACOBI_ERR_TIMEOUT in the status word if one runs out).  Results
- * are bit-identical to jacobi_sweep with T sweeps. */
+ * the grid is swept in items (x-y tile, z chunk of bz planes), and an item
+ * starts only after the items of its tile and the neighbouring tiles, in
+ * the two chunks whose input it overwrites (`waves` and waves+1 chunks
+ * back in sweep order), have finished (bounded waits: JACOBI_ERR_TIMEOUT in
+ * the status word if one runs out).  Results are bit-identical to
+ * jacobi_sweep with T sweeps. */
 
 /* Plan of the compressed sweeps: depth 1..4 sweeps per pass (FP32: the
  * register-blocked one-CTA body of JACOBI_KERNEL_TB_REG, 64 x 32 regions;
  * FP64: depth 1 only, else JACOBI_ERR_UNSUPPORTED), z chunk bz >= 2*depth+2,
- * waves 1..8 (JACOBI_ERR_ARG otherwise).  Default: FP32 depth 3, FP64 depth
- * 1; bz 64; waves 2. */
+ * waves 1..8 (JACOBI_ERR_ARG otherwise; the plan is then unchanged).  A zero
+ * field takes the default: FP32 depth 3, bz 128, waves 1 (S = 132); FP64
+ * depth 1, bz 64, waves 1 (S = 66). */
 int jacobi_compressed_set_plan(jacobi_h h, int depth, int bz, int waves);
 
 /* The current compressed plan and its shift S in planes (any may be NULL). */

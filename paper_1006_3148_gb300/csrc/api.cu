@@ -500,28 +500,41 @@ int jacobi_debug_set_fault(jacobi_h h, int mode, int limit_ms)
 int jacobi_build_checked(void) { return kChecked ? 1 : 0; }
 
 namespace {
-int cg_depth_of(const jacobi_plan_s *h) { return h->cg_depth > 0 ? h->cg_depth : (h->dtype == JACOBI_F64 ? 1 : 3); }
+// the compressed plan's defaults (measured on 1024^3 FP32 / 512^3 FP64)
+void cg_resolve(jacobi_plan_s *h)
+{
+    const bool f64 = h->dtype == JACOBI_F64;
+    if (h->cg_depth <= 0) h->cg_depth = f64 ? 1 : 3;
+    if (h->cg_bz <= 0) h->cg_bz = f64 ? 64 : 128;
+    if (h->cg_waves <= 0) h->cg_waves = 1;
+}
 }  // namespace
 
 int jacobi_compressed_set_plan(jacobi_h h, int depth, int bz, int waves)
 {
-    if (!h) return JACOBI_ERR_ARG;
-    const int st = cg_check(h, depth, bz, waves);
-    if (st != JACOBI_OK) return st;
-    h->cg_depth = depth;
+    if (!h || depth < 0 || bz < 0 || waves < 0) return JACOBI_ERR_ARG;
+    const int d0 = h->cg_depth, b0 = h->cg_bz, w0 = h->cg_waves;
+    h->cg_depth = depth;  // 0: the default, filled in below
     h->cg_bz = bz;
     h->cg_waves = waves;
-    return JACOBI_OK;
+    cg_resolve(h);
+    const int st = cg_check(h, h->cg_depth, h->cg_bz, h->cg_waves);
+    if (st != JACOBI_OK) {
+        h->cg_depth = d0;
+        h->cg_bz = b0;
+        h->cg_waves = w0;
+    }
+    return st;
 }
 
 int jacobi_compressed_get_plan(jacobi_h h, int *depth, int *bz, int *waves, long long *shift_planes)
 {
     if (!h) return JACOBI_ERR_ARG;
-    const int d = cg_depth_of(h);
-    if (depth) *depth = d;
+    cg_resolve(h);
+    if (depth) *depth = h->cg_depth;
     if (bz) *bz = h->cg_bz;
     if (waves) *waves = h->cg_waves;
-    if (shift_planes) *shift_planes = cg_shift_planes(d, h->cg_bz, h->cg_waves);
+    if (shift_planes) *shift_planes = cg_shift_planes(h->cg_depth, h->cg_bz, h->cg_waves);
     return JACOBI_OK;
 }
 
@@ -529,7 +542,7 @@ int jacobi_sweep_compressed(jacobi_h h, void *U, int T, int upper, int *upper_ou
 {
     if (!h || !U || T < 0 || (upper != 0 && upper != 1)) return JACOBI_ERR_ARG;
     if (!aligned16(U)) return JACOBI_ERR_ALIGN;
-    h->cg_depth = cg_depth_of(h);
+    cg_resolve(h);
     const int st = cg_check(h, h->cg_depth, h->cg_bz, h->cg_waves);
     if (st != JACOBI_OK) return st;
     return cg_sweep(h, U, T, upper, upper_out, (cudaStream_t)stream);

@@ -157,9 +157,9 @@ struct jacobi_plan_s {
     size_t ev_used = 0;
     int prof_pass = 0, prof_other = 0;
     long long check_shrink = 0;  // checked build test hook (jacobi_debug_set_fault mode 2)
-    // compressed grid: depth (0: 3 for FP32, 1 for FP64), z chunk, chunk
-    // waves; item ticket and per-chunk completion counters
-    int cg_depth = 0, cg_bz = 64, cg_waves = 2;
+    // compressed grid: depth, z chunk, chunk waves (0: the dtype's default,
+    // FP32 3 / 128 / 1, FP64 1 / 64 / 1); item ticket and per-item flags
+    int cg_depth = 0, cg_bz = 0, cg_waves = 0;
     int *cg_ctl = nullptr;
     size_t cg_ctl_n = 0;
     // Poisson / refinement scratch (allocated on first use, freed by destroy)

@@ -340,7 +340,8 @@ def jacobi_batch_get_engine(b: Batch) -> dict:
     return {"engine": e.value, "kz": kz.value}
 
 
-def jacobi_compressed_set_plan(h: Handle, depth: int, bz: int = 64, waves: int = 2):
+def jacobi_compressed_set_plan(h: Handle, depth: int = 0, bz: int = 0, waves: int = 0):
+    """Compressed-grid plan; a zero field takes the dtype's default."""
     _check(load().jacobi_compressed_set_plan(h.ptr, int(depth), int(bz), int(waves)), "jacobi_compressed_set_plan")
 
 

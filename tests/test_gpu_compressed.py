@@ -87,10 +87,10 @@ def test_fp64_compressed_bitwise():
 
 def test_compressed_defaults_zero_sweeps_and_sequential_oracle():
     h = J.Handle(20, 20, 20, torch.float32)
-    assert J.jacobi_compressed_get_plan(h) == {"depth": 3, "bz": 64, "waves": 2, "shift_planes": 2 * 64 + 3 + 1}
+    assert J.jacobi_compressed_get_plan(h) == {"depth": 3, "bz": 128, "waves": 1, "shift_planes": 128 + 3 + 1}
     h.close()
     h = J.Handle(20, 20, 20, torch.float64)
-    assert J.jacobi_compressed_get_plan(h)["depth"] == 1
+    assert J.jacobi_compressed_get_plan(h) == {"depth": 1, "bz": 64, "waves": 1, "shift_planes": 64 + 1 + 1}
     h.close()
     got, a = _run((40, 30, 50), torch.float32, 0)
     assert np.array_equal(got, a)
@@ -104,8 +104,11 @@ def test_compressed_argument_errors():
     h = J.Handle(16, 16, 16, torch.float32)
     assert L.jacobi_compressed_set_plan(h.ptr, 3, 7, 2) == -1   # bz < 2*depth + 2
     assert L.jacobi_compressed_set_plan(h.ptr, 5, 64, 2) == -1
-    assert L.jacobi_compressed_set_plan(h.ptr, 2, 64, 0) == -1
+    assert L.jacobi_compressed_set_plan(h.ptr, 2, 64, -1) == -1
     assert L.jacobi_compressed_set_plan(h.ptr, 2, 64, 9) == -1
+    assert J.jacobi_compressed_get_plan(h)["bz"] == 128        # unchanged by the refused plans
+    J.jacobi_compressed_set_plan(h, 2)                          # zero fields: the defaults
+    assert J.jacobi_compressed_get_plan(h) == {"depth": 2, "bz": 128, "waves": 1, "shift_planes": 131}
     U = J.compressed_buffer(h)
     assert L.jacobi_sweep_compressed(h.ptr, U.data_ptr(), 3, 2, None, None) == -1
     assert L.jacobi_sweep_compressed(h.ptr, U.data_ptr(), -1, 1, None, None) == -1

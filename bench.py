@@ -509,7 +509,7 @@ def run_ours(args, w, ctx, sub=False):
         del A, B
         torch.cuda.empty_cache()
         J.jacobi_profile_enable(h, False)
-        for _ in range(2):  # warm-up: device grids of the host entry point, pinned pages
+        for _ in range(max(2, args.warmup)):  # warm-up: device grids of the host entry point, pinned pages
             J.jacobi_sweep_host(h, host_in, host_out, T, stream)
         ctx.barrier()
         ke = max(1, min(args.steps, 3))
@@ -556,6 +556,8 @@ def run_batch(args, w, ctx, sub=False):
          for g, d in enumerate(dims)]
     B = [torch.empty_like(x) for x in A]
     tune = None
+    if args.batch_fp32_depth:
+        J.jacobi_batch_set_fp32_depth(b, args.batch_fp32_depth)
     if not args.no_tune:
         sa = [torch.empty_like(x) for x in A]
         sb = [torch.empty_like(x) for x in A]
@@ -811,6 +813,7 @@ def main():
     ap.add_argument("--plan", default=None, help="force a plan kernel:depth:bx:by:bz[:ring[:threads]], kernel tb, cta, "
                     "reg, chain (ring = CTAs), plain or x2, e.g. tb:4:64:16:64:8, cta:4:64:32:64:0:512 or x2:1:32:8:16")
     ap.add_argument("--cg-plan", default=None, help="compressed grid plan depth:bz:waves")
+    ap.add_argument("--batch-fp32-depth", type=int, default=0, help="FP32 depth of the batch (with --no-tune)")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -13,7 +13,7 @@ namespace jac {
 namespace {
 
 template <int D, int A>
-__global__ void __launch_bounds__(128, (TbrMinBlocks<D, 128>::value))
+__global__ void __launch_bounds__(128, (TbrMinBlocks<D, 128, A>::value))
     tbr_batch_kernel(const BatchGrid *grids, const TbrBatchEntry *tab, int n, int pass, int *status, long long shrink)
 {
     const long long b = blockIdx.x;

@@ -144,30 +144,29 @@ __device__ void finish_item(const CgArgs &a, long long q, int c, int j)
     }
 }
 
-// Copies the Dirichlet cells of tile (tix, tiy)'s footprint from the read
-// position to the write position: the x-y ring cells of planes [z0, z1) and,
-// for the first / last chunk, every footprint cell of plane 0 / nz+1.
+// Copies the Dirichlet cells of a tile's footprint, columns [fx0, fx1) x
+// rows [fy0, fy1), from the read position to the write position: the x-y
+// ring cells of planes [z0, z1) and, for the first / last chunk, every
+// footprint cell of plane 0 / nz+1.  Out of line, with its operands by
+// value (a reference to the kernel's parameters would move them to local
+// memory for the whole kernel).
 template <typename T>
-__device__ __noinline__ void move_boundary(const CgArgs &a, int tix, int tiy, int z0, int z1, bool first, bool last)
+__device__ __noinline__ void move_boundary(const T *src, T *dst, int nx, int ny, int nz, int fx0, int fx1, int fy0,
+                                           int fy1, int z0, int z1, bool first, bool last, int *status,
+                                           long long shrink)
 {
-    const T *src = static_cast<const T *>(a.src);
-    T *dst = static_cast<T *>(a.dst);
-    const long long P = a.nx + 2, plane = P * (a.ny + 2);
-    const long long SG = checked_grid_elems(a.nx, a.ny, a.nz, a.shrink);
-    const int fx0 = tix == 0 ? 0 : a.fx0 + tix * a.fbx;
-    const int fx1 = tix == a.ntx - 1 ? a.nx + 2 : a.fx0 + (tix + 1) * a.fbx;
-    const int fy0 = tiy == 0 ? 0 : 1 + tiy * a.fby;
-    const int fy1 = tiy == a.nty - 1 ? a.ny + 2 : 1 + (tiy + 1) * a.fby;
+    const long long P = nx + 2, plane = P * (ny + 2);
+    const long long SG = checked_grid_elems(nx, ny, nz, shrink);
     const int w = fx1 - fx0, h = fy1 - fy0;
     auto mv = [&](long long off) {
-        if (in_bounds(off, 1, SG, a.status)) dst[off] = __ldcg(src + off);
+        if (in_bounds(off, 1, SG, status)) dst[off] = __ldcg(src + off);
     };
     for (int e = 0; e < 2; ++e) {
         if (!(e == 0 ? first : last)) continue;
-        const long long pz = (e == 0 ? 0 : a.nz + 1) * plane;
+        const long long pz = (e == 0 ? 0 : nz + 1) * plane;
         for (int i = threadIdx.x; i < w * h; i += blockDim.x) mv(pz + (long long)(fy0 + i / w) * P + fx0 + i % w);
     }
-    const int yl = fy0 == 0, yr = fy1 == a.ny + 2, xl = fx0 == 0, xr = fx1 == a.nx + 2;
+    const int yl = fy0 == 0, yr = fy1 == ny + 2, xl = fx0 == 0, xr = fx1 == nx + 2;
     const int nrow = (yl + yr) * w, ncol = (xl + xr) * (h - yl - yr);
     const int per = nrow + ncol;
     if (per == 0) return;
@@ -177,18 +176,35 @@ __device__ __noinline__ void move_boundary(const CgArgs &a, int tix, int tiy, in
         int x, y;
         if (r < nrow) {
             x = fx0 + r % w;
-            y = (yl && r < w) ? 0 : a.ny + 1;
+            y = (yl && r < w) ? 0 : ny + 1;
         } else {
             const int k = r - nrow, hh = h - yl - yr;
             y = fy0 + yl + k % hh;
-            x = (xl && k < hh) ? 0 : a.nx + 1;
+            x = (xl && k < hh) ? 0 : nx + 1;
         }
         mv(p * plane + (long long)y * P + x);
     }
 }
 
+// The footprint of tile (tix, tiy) and the boundary move of item (tile, j).
+template <typename T>
+__device__ __forceinline__ void move_item_boundary(const CgArgs &a, int tix, int tiy, int j)
+{
+    const int fx0 = tix == 0 ? 0 : a.fx0 + tix * a.fbx;
+    const int fx1 = tix == a.ntx - 1 ? a.nx + 2 : a.fx0 + (tix + 1) * a.fbx;
+    const int fy0 = tiy == 0 ? 0 : 1 + tiy * a.fby;
+    const int fy1 = tiy == a.nty - 1 ? a.ny + 2 : 1 + (tiy + 1) * a.fby;
+    const int z0 = 1 + j * a.bz, z1 = min(z0 + a.bz, a.nz + 1);
+    const bool first = j == 0, last = j == a.nch - 1;
+    // only footprints on the grid's x-y boundary, and the first and last
+    // chunks, hold Dirichlet cells
+    if (!(first || last || fx0 == 0 || fy0 == 0 || fx1 == a.nx + 2 || fy1 == a.ny + 2)) return;
+    move_boundary<T>(static_cast<const T *>(a.src), static_cast<T *>(a.dst), a.nx, a.ny, a.nz, fx0, fx1, fy0, fy1, z0,
+                     z1, first, last, a.status, a.shrink);
+}
+
 template <int D, int A>
-__global__ void __launch_bounds__(128, (TbrMinBlocks<D, 128>::value)) cg_f32_kernel(const CgArgs a)
+__global__ void __launch_bounds__(128, (TbrMinBlocks<D, 128, A>::value)) cg_f32_kernel(const CgArgs a)
 {
     long long q;
     int c, j;
@@ -197,8 +213,7 @@ __global__ void __launch_bounds__(128, (TbrMinBlocks<D, 128>::value)) cg_f32_ker
     if (ok) {
         const int tix = c % a.ntx, tiy = c / a.ntx;
         tbr_cta<D, 16, 8, A>(a.t, tix, tiy, j);
-        const int z0 = 1 + j * a.bz, z1 = min(z0 + a.bz, a.nz + 1);
-        move_boundary<float>(a, tix, tiy, z0, z1, j == 0, j == a.nch - 1);
+        move_item_boundary<float>(a, tix, tiy, j);
     }
     finish_item(a, q, c, j);
 }
@@ -240,7 +255,7 @@ __global__ void __launch_bounds__(kCgF64X *kCgF64Y) cg_f64_kernel(const CgArgs a
                 o += plane;
             }
         }
-        move_boundary<double>(a, tix, tiy, z0, z1, j == 0, j == a.nch - 1);
+        move_item_boundary<double>(a, tix, tiy, j);
     }
     finish_item(a, q, c, j);
 }

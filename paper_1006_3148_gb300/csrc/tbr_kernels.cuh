@@ -123,11 +123,13 @@ __device__ __forceinline__ void tbr_block_update(const float (&cur)[kTbrVY][4], 
     }
 }
 
-// Resident CTAs requested per SM: three 128-thread CTAs at depth <= 2 (at
-// most 170 registers, which those depths fit without spilling), else one.
-template <int D, int NT>
+// Resident CTAs requested per SM: three 128-thread CTAs at depth 1, and at
+// depth 2 with copy pieces of two cells (at most 170 registers, which those
+// fit without spilling); two at depth 2 with single-cell pieces (whose
+// address arithmetic spills at 170); else one.
+template <int D, int NT, int A>
 struct TbrMinBlocks {
-    static constexpr int value = (NT == 128 && D <= 2) ? 3 : 1;
+    static constexpr int value = (NT == 128 && (D == 1 || (D == 2 && A == 2))) ? 3 : (NT == 128 && D == 2) ? 2 : 1;
 };
 
 // The work of one CTA: tile (tix, tiy) in x and y, z chunk tiz.
@@ -397,7 +399,7 @@ __device__ __forceinline__ void tbr_cta(const TbrArgs &a, int tix, int tiy, int 
 }
 
 template <int D, int TX, int TY, int A>
-__global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY>::value)) tbr_pass_kernel(const TbrArgs a)
+__global__ void __launch_bounds__(TX *TY, (TbrMinBlocks<D, TX * TY, A>::value)) tbr_pass_kernel(const TbrArgs a)
 {
     tbr_cta<D, TX, TY, A>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
 }

@@ -62,6 +62,7 @@ MEASURED_TRAFFIC = {
     ("tbc4_pass_kernel", "f32", 2): (3.97, "ncu: tbc4_pass_kernel depth 2, FP32 512^3"),
     ("tbc4_pass_kernel", "f32", 4): (2.04, "ncu: tbc4_pass_kernel depth 4, FP32 512^3"),
     ("tbr_pass_kernel", "f32", 3): (2.82, "ncu: tbr_pass_kernel depth 3, region 64x32, FP32 512^3, one pass"),
+    ("cg_f32_kernel", "f32", 3): (3.05, "ncu: cg_f32_kernel depth 3, 128-plane chunks, FP32 512^3, one pass"),
 }
 SM_MAX_MHZ = 2070.0
 
@@ -723,6 +724,11 @@ def run_compressed(args, w, ctx, sub=False):
             "avg_launch_ms": pass_ms,
             "note": "algorithmic bytes: read and write the grid once per pass (2 x %d B per cell); pass time = "
                     "step time / passes (one launch per pass and a counter reset)" % es}
+    measured = MEASURED_TRAFFIC.get((roof["kernel"], w["dtype"], cg["depth"]))
+    if measured is not None and cg["bz"] == 128:
+        # bytes per LUP of the captured launch x the LUPs of one pass here
+        roof["traffic"] = measured[0] * nx * ny * nz * cg["depth"]
+        roof["traffic_source"] = measured[1] + " (bytes per LUP x LUPs of this pass)"
     grid_bytes = (nx + 2) * (ny + 2) * (nz + 2) * es
     line = {
         "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": ws, "steps": args.steps,

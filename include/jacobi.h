@@ -111,7 +111,10 @@ int jacobi_destroy(jacobi_h h);
  * with single sweeps; the other grid's interior is left unspecified.  T = 0
  * does nothing.  A and B: device pointers, 16-byte aligned, not
  * overlapping, each (nx+2)(ny+2)(nz+2) elements.  Asynchronous on stream.
- * Device-side wait timeouts are reported by jacobi_get_status. */
+ * Device-side wait timeouts are reported by jacobi_get_status.  Once a call
+ * with the same plan has run uncaptured (it sets the kernels' shared-memory
+ * limits), the call enqueues kernel launches only and can be captured into
+ * a CUDA graph. */
 int jacobi_sweep(jacobi_h h, void *A, void *B, int T, jacobi_stream_t stream);
 
 /* Same operation with host buffers (end-to-end entry point): copies
@@ -339,8 +342,9 @@ int jacobi_compressed_get_plan(jacobi_h h, int *depth, int *bz, int *waves, long
  * does not divide T); *upper_out (may be NULL) receives the position of the
  * result: upper XOR (number of passes odd).  Cells of U outside the grid's
  * position are scratch.  Asynchronous on stream; allocates its small
- * counter array on first use (kept on the handle).  Calls on one handle
- * must not overlap. */
+ * counter array on first use (kept on the handle); after one uncaptured
+ * call, a call enqueues memsets and kernel launches only and can be
+ * captured into a CUDA graph.  Calls on one handle must not overlap. */
 int jacobi_sweep_compressed(jacobi_h h, void *U, int T, int upper, int *upper_out, jacobi_stream_t stream);
 
 /* ---------------------------------------------------------------- batch
@@ -369,7 +373,9 @@ int jacobi_batch_create(jacobi_batch_h *out, int n, const int *nx, const int *ny
 /* Binds the grids and launches the graph on stream.  A, B: host arrays of
  * n device pointers (grid g: (nx+2)(ny+2)(nz+2) elements of its dtype,
  * A[g] != B[g]); the pointer table is copied to the device on stream before
- * the graph launch.  Asynchronous.  Runs of one batch must not overlap. */
+ * the graph launch.  Asynchronous.  Runs of one batch must not overlap.
+ * Not for stream capture: the call launches the batch's own graph after a
+ * copy from host memory. */
 int jacobi_batch_run(jacobi_batch_h b, void *const *A, void *const *B, jacobi_stream_t stream);
 
 /* Same, for the Poisson problem -Lap_h u = f: grid g is swept with the

@@ -315,6 +315,42 @@ int run_sweeps(jacobi_plan_s *h, const Plan &p, void *A, void *B, int T, cudaStr
 
 }  // namespace
 
+namespace jac {
+namespace {
+std::mutex g_attr_mu;
+std::map<std::pair<const void *, int>, size_t> g_smem_set;  // (kernel, device) -> limit set
+std::map<std::pair<const void *, int>, int> g_cluster_set;   // (kernel, device) -> smem_max set
+}  // namespace
+
+cudaError_t ensure_smem_limit(const void *fn, size_t smem)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    size_t &cur = g_smem_set[std::make_pair(fn, dev)];
+    if (smem <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) cur = smem;
+    return e;
+}
+
+cudaError_t ensure_cluster_attrs(const void *fn, int smem_max)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    int &cur = g_cluster_set[std::make_pair(fn, dev)];
+    if (cur >= smem_max) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) cur = smem_max;
+    return e;
+}
+}  // namespace jac
+
 extern "C" {
 
 const char *jacobi_status_string(int status)

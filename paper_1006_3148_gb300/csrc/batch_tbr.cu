@@ -59,7 +59,7 @@ cudaError_t launch(const TbrBatchLaunch &L, const BatchGrid *d_grids, const TbrB
 {
     auto fn = tbr_batch_kernel<D, A>;
     const size_t smem = smem_bytes<D>();
-    if (configure) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (configure) return ensure_smem_limit((const void *)fn, smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)L.units);
     cfg.blockDim = dim3(128);

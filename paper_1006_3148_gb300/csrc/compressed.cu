@@ -265,7 +265,7 @@ cudaError_t launch_f32(const CgArgs &a, cudaStream_t s)
 {
     auto fn = cg_f32_kernel<D, A>;
     const size_t smem = ((size_t)tbr_ring(D) * 64 * 32 + 2 * (size_t)D * (2 * 8 * 64 + 2 * 8 * 16 * kTbrVY)) * 4;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_limit((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     fn<<<(unsigned)a.items, 128, smem, s>>>(a);
     return cudaGetLastError();

@@ -173,6 +173,15 @@ struct jacobi_plan_s {
 };
 
 namespace jac {
+// Raises fn's dynamic shared memory limit on the current device to at least
+// smem bytes.  The attribute call is made only when the limit grows (once
+// per kernel and device in practice), so the launches that follow are plain
+// stream work and can be captured into a CUDA graph.
+cudaError_t ensure_smem_limit(const void *fn, size_t smem);
+// The cluster kernels' attributes (largest dynamic shared memory, full
+// shared-memory carveout, clusters above 8 CTAs), set once per kernel and
+// device.
+cudaError_t ensure_cluster_attrs(const void *fn, int smem_max);
 void free_poisson_scratch(jacobi_plan_s *h);
 // compressed grid (compressed.cu)
 long long cg_shift_planes(int depth, int bz, int waves);

@@ -250,14 +250,7 @@ const void *tb_kernel(int dtype, int nc, int maxc)
     return f;
 }
 
-cudaError_t prepare(const void *fn)
-{
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-}
+cudaError_t prepare(const void *fn) { return ensure_cluster_attrs(fn, kSmemMax); }
 
 }  // namespace
 

@@ -326,7 +326,7 @@ cudaError_t launch_quad(const TbcArgs &a, cudaStream_t s)
 {
     auto fn = tbc4_pass_kernel<D, NT, QPT>;
     const size_t smem = (size_t)(kRing + 2 * (D - 1)) * a.WH * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_limit((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((a.nx + a.bx - 1) / a.bx), (unsigned)((a.ny + a.by - 1) / a.by),
               (unsigned)((a.nz + a.bz - 1) / a.bz));
@@ -362,7 +362,7 @@ cudaError_t launch_one(const TbcArgs &a, cudaStream_t s)
 {
     auto fn = tbc_pass_kernel<T, D, NT, CPT>;
     const size_t smem = (size_t)(kRing + 2 * (D - 1)) * a.WH * sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_limit((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((a.nx + a.bx - 1) / a.bx), (unsigned)((a.ny + a.by - 1) / a.by),
               (unsigned)((a.nz + a.bz - 1) / a.bz));

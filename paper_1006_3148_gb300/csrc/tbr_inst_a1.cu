@@ -11,7 +11,7 @@ template <int D, int TX, int TY>
 cudaError_t launch(const TbrArgs &a, size_t smem, cudaStream_t s)
 {
     auto fn = tbr_pass_kernel<D, TX, TY, 1>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_limit((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((a.nx + a.bx - 1) / a.bx), (unsigned)((a.ny + a.by - 1) / a.by),

@@ -83,7 +83,7 @@ cudaError_t tbx_launch(int depth, int cluster, int W, int H, const TbxArgs &a0, 
     if (tbx_configure(depth, cluster, W, H, &a, &smem) != JACOBI_OK) return cudaErrorInvalidValue;
     const int tm = max_levels(depth, cluster) <= 2 ? 2 : 4;
     const void *fn = pick(tm, W, H, (a.nx + 2) % 2 == 0 ? 2 : 1);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_limit(fn, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = config(a, W, H, smem, attr);
@@ -103,7 +103,7 @@ cudaError_t tbx_max_clusters(int depth, int cluster, int W, int H, int nx, int *
     if (tbx_configure(depth, cluster, W, H, &a, &smem) != JACOBI_OK) return cudaErrorInvalidValue;
     const int tm = max_levels(depth, cluster) <= 2 ? 2 : 4;
     const void *fn = pick(tm, W, H, (nx + 2) % 2 == 0 ? 2 : 1);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_limit(fn, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = config(a, W, H, smem, attr);

@@ -71,6 +71,10 @@ WORKLOADS = {
                      name="jacobi3d_fp64_512cubed_T100_z0face1"),
     "fp64_64": dict(n=(64, 64, 64), dtype="f64", T=10, gen="uniform", seed=1,
                     name="jacobi3d_fp64_64cubed_T10"),
+    # the paper's grid shape (Sect. 2.3: a 600^3 domain; its values are not
+    # given), as a context configuration
+    "fp64_600": dict(n=(600, 600, 600), dtype="f64", T=100, gen="uniform", seed=6,
+                     name="jacobi3d_fp64_600cubed_T100_paper_shape"),
     "fp32_1024": dict(n=(1024, 1024, 1024), dtype="f32", T=200, gen="mode", seed=3,
                       name="jacobi3d_fp32_1024cubed_T200_mode16"),
     "compressed1024": dict(n=(1024, 1024, 1024), dtype="f32", T=200, gen="mode", seed=3,

@@ -11,10 +11,11 @@
 // position and writes the result into the other: an upper-to-lower pass
 // overwrites planes that held its own input S planes further down.
 //
-// Work items are (x-y tile, z chunk of bz planes), one CTA each.  Item (t, j) reads input
-// planes [z0_j - D, z0_j + bz + D) and writes output planes [z0_j, z0_j + bz)
-// (plus the boundary plane 0 or nz+1 for the first and last chunks), i.e.
-// input planes [z0_j - S, z0_j - S + bz + 1) in an upper-to-lower pass.  With
+// Work items are (x-y tile, z chunk of bz planes), one CTA each.  Item
+// (t, j) reads input planes [z0_j - D, z0_j + bz + D) and writes output
+// planes [z0_j, z0_j + bz) (plus the boundary plane 0 or nz+1 for the first
+// and last chunks), i.e. input planes [z0_j - S, z0_j - S + bz + 1) in an
+// upper-to-lower pass.  With
 // S = w*bz + D + 1 and bz >= 2D + 2 those are read only by the items of
 // chunks j-w and j-w-1, and among them (the x-y regions reach D cells, less
 // than a tile, past their tile) only by the items of tile t and its eight

@@ -232,9 +232,9 @@ int jacobi_profile_read(jacobi_h h, double *pass_ms, int *pass_launches, int *ot
 
 /* Test hook for failure detection: mode 1 makes the next pass kernel omit
  * one mbarrier arrival (TB: a cp.async arrival; TB_CHAIN: the first CTA's
- * hand-off of one plane) so that its bounded waits run out (after
- * limit_ms milliseconds); the kernel records JACOBI_ERR_TIMEOUT and returns
- * without faulting.  Mode 2 (bounds-checked build only, else
+ * hand-off of one plane; the compressed grid: the first item's completion
+ * flag) so that its bounded waits run out (after limit_ms milliseconds);
+ * the kernel records JACOBI_ERR_TIMEOUT and returns without faulting.  Mode 2 (bounds-checked build only, else
  * JACOBI_ERR_UNSUPPORTED): the kernels check their accesses against grids
  * declared one element shorter than they are, so the accesses to each
  * grid's last element are reported as JACOBI_ERR_BOUNDS and skipped (every

@@ -342,9 +342,11 @@ int jacobi_compressed_get_plan(jacobi_h h, int *depth, int *bz, int *waves, long
  * does not divide T); *upper_out (may be NULL) receives the position of the
  * result: upper XOR (number of passes odd).  Cells of U outside the grid's
  * position are scratch.  Asynchronous on stream; allocates its small
- * counter array on first use (kept on the handle); after one uncaptured
- * call, a call enqueues memsets and kernel launches only and can be
- * captured into a CUDA graph.  Calls on one handle must not overlap. */
+ * counter array on first use, and a larger one when a plan needs more
+ * (kept on the handle, the replaced ones too, until jacobi_destroy); after
+ * one uncaptured call with the plan, a call enqueues memsets and kernel
+ * launches only and can be captured into a CUDA graph, which stays valid
+ * until the handle is destroyed.  Calls on one handle must not overlap. */
 int jacobi_sweep_compressed(jacobi_h h, void *U, int T, int upper, int *upper_out, jacobi_stream_t stream);
 
 /* ---------------------------------------------------------------- batch

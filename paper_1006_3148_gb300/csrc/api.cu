@@ -421,6 +421,7 @@ int jacobi_destroy(jacobi_h h)
     if (h->hostB) cudaFree(h->hostB);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->cg_ctl) cudaFree(h->cg_ctl);
+    for (int *p : h->cg_old) cudaFree(p);
     free_poisson_scratch(h);
     delete h;
     return JACOBI_OK;

@@ -347,10 +347,12 @@ int cg_sweep(jacobi_plan_s *h, void *U, int T, int upper, int *upper_out, cudaSt
     if (a.items >= (1ll << 31) || (long long)a.ntx * a.nty >= (1ll << 31)) return JACOBI_ERR_UNSUPPORTED;
     const size_t need = 1 + (size_t)nch * a.ntx * a.nty;
     if (h->cg_ctl_n < need) {
-        if (h->cg_ctl) cudaFree(h->cg_ctl);
-        h->cg_ctl = nullptr;
-        h->cg_ctl_n = 0;
-        if (cudaMalloc(&h->cg_ctl, need * sizeof(int)) != cudaSuccess) return JACOBI_ERR_ALLOC;
+        // a CUDA graph captured from an earlier call may still use the old
+        // array: it is kept until the handle is destroyed
+        int *p = nullptr;
+        if (cudaMalloc(&p, need * sizeof(int)) != cudaSuccess) return JACOBI_ERR_ALLOC;
+        if (h->cg_ctl) h->cg_old.push_back(h->cg_ctl);
+        h->cg_ctl = p;
         h->cg_ctl_n = need;
     }
     a.head = h->cg_ctl;

@@ -162,6 +162,7 @@ struct jacobi_plan_s {
     int cg_depth = 0, cg_bz = 0, cg_waves = 0;
     int *cg_ctl = nullptr;
     size_t cg_ctl_n = 0;
+    std::vector<int *> cg_old;  // replaced counter arrays, kept for captured graphs until destroy
     // Poisson / refinement scratch (allocated on first use, freed by destroy)
     void *g = nullptr;          // source term h^2 r (FP32) or h^2 f (FP64)
     void *e0 = nullptr, *e1 = nullptr;  // FP32 correction grids

@@ -1,5 +1,6 @@
 """Host-side pieces of bench.py that need no GPU: the CPU-oracle baseline
-(all cores and one core) on a small workload grid."""
+(all cores and one core) on a small workload grid, the workloads' config
+keys shared by both arms, and the reference arm's line."""
 import bench
 import oracle
 
@@ -25,3 +26,32 @@ def test_oracle_thread_count_does_not_change_results():
     finally:
         oracle.set_threads(n)
     assert np.array_equal(r1, r2)
+
+
+def test_every_workload_has_one_config_for_both_arms():
+    # both arms build config with the same function of the workload, so the
+    # driver's ratio compares like with like
+    for key, w in bench.WORKLOADS.items():
+        w = dict(w)
+        if w["gen"] == "batch":
+            c = bench.batch_config(w, 1)
+        elif w["gen"] == "poisson":
+            c = bench.poisson_config(w, 1)
+        else:
+            c = bench.grid_config(w, 1)
+        assert c["workload"] == w["name"], key
+        assert c["parallelism"] == "single"
+
+
+def test_reference_arm_line_on_a_small_workload(capsys):
+    import argparse
+    import json
+    args = argparse.Namespace(gpus=1, steps=2, warmup=1, impl="reference", workload="fp64_64", cpu_budget=1.0,
+                              no_cpu_baseline=False)
+    w = dict(bench.WORKLOADS["fp64_64"])
+    line = bench.run_reference(args, w)
+    assert line["impl"] == "reference" and line["unit"] == "GLUP/s" and line["higher_is_better"] is True
+    assert line["config"] == bench.grid_config(w, 1)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+    json.dumps(line)
